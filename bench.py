@@ -1,0 +1,311 @@
+"""Benchmark of the batched Hermite-Fourier split step.
+
+Workload (one bench "step"): one batched solve of 4096 independent 1D GPE
+instances of mixed grid size N ~ U{128,...,4096} (half-width 8 + N/64,
+omega(t) = omega0 (1 + 0.3 sin t), omega0 ~ U[0.5,2], sigma ~ U[-1,20],
+eps ~ U[0,0.1], V_I = cos(kx), k ~ U[1,4], Gaussian psi0 of width
+1/sqrt(omega0) at x0 ~ U[-1,1]), 500 Strang steps of dt = 0.005 with the
+commutator-free Magnus-4 + Theorem-2 harmonic flow, complex64 -- one
+hfs_step(500) call, replayed from a captured CUDA graph.
+
+Metric: grid-point-steps per second (sum over instances of N x time steps).
+Between timed steps a 256 MiB buffer is written to flush L2 (outside the
+per-step CUDA events).  ``e2e`` repeats the solve through the public C ABI
+with host buffers: host->device copy of psi0 from pinned memory, the solve,
+device->host copy of psi(T), all inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the slow, plain
+stage-by-stage implementation the tests compare with) on a bounded,
+stratified sample of the same workload.
+
+Multi-GPU (torchrun): every rank solves its own 4096-instance batch (seed
+offset by the rank) with no data-path communication; value = all ranks'
+grid-point-steps / max over ranks of the timed span ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point-steps/s"
+COUNT, STEPS, DT = 4096, 500, 0.005
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_counts(insts, steps):
+    """Per solve: grid-point-steps, algorithmic flops and streaming bytes.
+
+    flops per grid-point-step: 10 log2 N (forward + inverse FFT, radix-2
+    count 5 N log2 N each) + 22 (two complex phase multiplies of 6 flops,
+    the merged phase argument kappa x^2/2 + s (eps V_I + sigma |u|^2) with
+    |u|^2 and 7 more, and the kinetic argument g k^2/2 with 3); the two
+    sine/cosine pairs per point-step are not counted as flops."""
+    pts = np.array([i.n[0] for i in insts], dtype=np.float64)
+    gps = float(pts.sum() * steps)
+    flops = float(np.sum(pts * (10.0 * np.log2(pts) + 22.0)) * steps)
+    return gps, flops
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1007_3470_gb300 import hfs
+    from paper_1007_3470_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    insts, psis, _ = W.batch_1d(count=COUNT, seed=W.SEED + rank, h=DT, steps=STEPS)
+    gps, flops = algorithmic_counts(insts, STEPS)
+    solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS)
+    solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    tuned = solver.autotune(trial_steps=20) if args.autotune else None
+    solver.set_graphs(True)
+    host0 = np.concatenate([p.astype(np.complex64) for p in psis])
+    pinned_in = torch.from_numpy(host0.view(np.float32)).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    solver.set_psi(host0)
+    stream = solver.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one():
+        solver.step(STEPS)
+
+    for _ in range(args.warmup):
+        one()
+    stream.synchronize()
+    # device-timed value: per-step CUDA events on the solver's stream, L2 flushed between steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            one()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(ms)
+    st = solver.status()
+    # the dominant kernel: one resident launch per solve (all 500 steps on chip)
+    step_ms = total_ms / args.steps
+    # end to end through the C ABI with host buffers
+    e2e_ms = []
+    for k in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hfs.hfs_set_psi(solver.h, pinned_in.data_ptr(), False)
+        solver.step(STEPS)
+        hfs.hfs_get_psi(solver.h, pinned_out.data_ptr(), False)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step_ms = statistics.median(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms, e2e_step_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_step_ms = float(t[0]), float(t[1])
+    value = gps * ws * args.steps / (total_ms * 1e-3)
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved_tflops = flops / (step_ms * 1e-3) / 1e12
+    hbm_equiv = gps * 16.0 / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+        "config": {"workload": "batch_1d_4096x500_c64", "instances": COUNT, "time_steps": STEPS, "dt": DT,
+                   "grid_sizes": "128..4096 uniform", "composition": "strang", "ho_flow": "magnus4_cf+thm2",
+                   "mode": "resident, graph-replayed", "l2": "flushed between steps (256 MiB write)",
+                   "solves_per_s": ws * args.steps / (total_ms * 1e-3),
+                   "plans_ept": tuned},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / alu_peak, "traffic": None,
+                     "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz {src})",
+                     "hbm_equivalent_GBps": hbm_equiv, "hbm_equivalent_frac_of_measured": hbm_equiv / hbm},
+        "e2e": {"value": gps * ws / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
+                "h2d_bytes_per_step": int(host0.nbytes), "d2h_bytes_per_step": int(host0.nbytes)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+        "status": st,
+        "wall_s": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _stratified_sample(per_size: int, seed: int):
+    from paper_1007_3470_gb300 import workloads as W
+    insts, psis, _ = W.batch_1d(count=COUNT, seed=seed, h=DT, steps=STEPS)
+    pick, seen = [], {}
+    for i, inst in enumerate(insts):
+        n = inst.n[0]
+        if seen.get(n, 0) < per_size:
+            seen[n] = seen.get(n, 0) + 1
+            pick.append(i)
+    return [insts[i] for i in pick], [psis[i] for i in pick]
+
+
+def cpu_baseline(per_size: int):
+    """The FP64 oracle, as it stands, on a stratified sample of the workload
+    (per_size instances of every grid size, all 500 steps), OpenMP over
+    instances on every host core."""
+    from oracle import oracle as O
+    insts, psis = _stratified_sample(per_size, 20100703)
+    probs = [O.Problem(**i.as_dict()) for i in insts]
+    cores = O.max_threads()
+    t0 = time.perf_counter()
+    O.run_batch(probs, psis, STEPS, cores)
+    dt = time.perf_counter() - t0
+    gps = sum(i.n[0] for i in insts) * STEPS
+    return {"value": gps / dt, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(insts)} instances ({per_size} per grid size 128..4096) x {STEPS} steps, "
+                      f"FP64 stage-by-stage oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; each step below is a full bounded sample
+    insts, psis = _stratified_sample(args.cpu_sample, 20100703)
+    probs = [O.Problem(**i.as_dict()) for i in insts]
+    cores = O.max_threads()
+    gps = sum(i.n[0] for i in insts) * STEPS
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.run_batch(probs, psis, STEPS, cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = gps * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": "batch_1d_4096x500_c64", "instances": COUNT, "time_steps": STEPS, "dt": DT,
+                   "sample_per_step": f"{len(insts)} instances stratified over grid sizes"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(insts)} instances ({args.cpu_sample} per grid size) x {STEPS} steps per step"},
+        "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="instances per grid size in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_1007_3470_gb300 import build as B
+        B.build()
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * hfs.h -- C ABI of the GB300 (sm_103a) Hermite-Fourier split-step library.
+ *
+ * The library advances the 1D or 3D Gross-Pitaevskii / linear Schrodinger
+ * equation with a perturbed, possibly time-dependent harmonic trap,
+ *     i psi_t = ( p^2/(2 mu) + mu omega^2(t) x^2 / 2 ) psi
+ *               + ( eps V_I(x) + sigma |psi|^2 ) psi                (Eq. GP1, GP1b)
+ * on a periodic grid x_j = lo + j dx, dx = (hi - lo)/N (Eq. GP1ODE), by the
+ * Hermite-Fourier splitting of Bader & Blanes (arXiv 1007.3470, Sec. 3):
+ * each A stage (the harmonic flow, exact by Lemma 2 or Magnus-approximated
+ * by Eq. CommutatorFree / the sixth-order Magnus of Sec. 4.2) is written as
+ * chirp . kinetic . chirp (Theorems 1, 2), and composed with the pointwise
+ * flow of eps V_I + sigma |psi|^2 (Lemma 1) by the m-stage compositions of
+ * Eq. prod-gen / Table 1 with the frozen-time algorithm of Table
+ * "algorithm"; adjacent chirps and B flows are merged as in
+ * Eq. prod-genHarmOsc, so one step costs m forward + m inverse FFTs.
+ *
+ * Conventions for every entry point:
+ *  - All functions return an int status (HFS_OK == 0); nothing throws or
+ *    aborts across the ABI.  hfs_error_string() names a status.
+ *  - The library performs NO device allocation.  The caller owns the state
+ *    buffer psi and the workspace (e.g. torch tensors) and binds them with
+ *    hfs_bind(); their sizes come from hfs_state_size() and
+ *    hfs_workspace_size().  Both must stay valid until hfs_destroy() or the
+ *    next hfs_bind().  The context itself is a small host allocation.
+ *  - Device work is enqueued asynchronously on the stream given to
+ *    hfs_set_stream() (default: the legacy default stream).  Calls that
+ *    return host data (hfs_norm, hfs_energy, hfs_get_psi to host,
+ *    hfs_sync_status) synchronise that stream.
+ *  - psi is interleaved complex: complex64 (2 x float) for HFS_C64 or
+ *    complex128 (2 x double) for HFS_C128.  A 1D batch is the concatenation
+ *    of its instances in order (offsets from hfs_instance_offset()); a 3D
+ *    instance is row-major with axis 0 (x) fastest.
+ *  - Asynchronous device-side problems (non-finite coefficients, an
+ *    exhausted bounded wait) are recorded in a device status word that
+ *    hfs_sync_status() reads and clears.
+ */
+#ifndef HFS_H
+#define HFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HFS_API_VERSION 1
+
+/* ---- status codes ------------------------------------------------------ */
+#define HFS_OK 0
+#define HFS_ERR_INVALID_ARG 1    /* null pointer, bad enum, bad size */
+#define HFS_ERR_UNSUPPORTED 2    /* grid size / dim / precision not built */
+#define HFS_ERR_STEP_TOO_LARGE 3 /* |a_i h| omega_max >= pi: outside the validity of Lemma 2 / Thms 1-2 */
+#define HFS_ERR_CUDA 4           /* a CUDA runtime call failed */
+#define HFS_ERR_NONFINITE 5      /* non-finite coefficient or state detected */
+#define HFS_ERR_NOT_READY 6      /* buffers not bound or schedule not set */
+#define HFS_ERR_ALIGNMENT 7      /* psi or workspace not 256-byte aligned */
+#define HFS_ERR_WORKSPACE 8      /* bound workspace smaller than required */
+#define HFS_ERR_DEVICE_TIMEOUT 9 /* a bounded device-side wait ran out */
+
+/* ---- enums ------------------------------------------------------------- */
+#define HFS_C64 0  /* complex64 state, FP32 bulk arithmetic */
+#define HFS_C128 1 /* complex128 state, FP64 throughout (parity mode) */
+
+/* omega(t) of Eq. GP1b; per axis omega_d = axis_scale[d] * omega in 3D */
+#define HFS_OMEGA_CONST 0  /* omega = w0 */
+#define HFS_OMEGA_SIN 1    /* omega = w0 (1 + law[0] sin(law[1] t + law[2])) */
+#define HFS_OMEGA_COS_SQ 2 /* omega^2 = w0^2 (1 + law[0] cos(law[1] t))   (Sec. 4.2) */
+#define HFS_OMEGA_PULSE 3  /* omega = w0 (1 + law[0] t / cosh^2(law[1] (t - law[2])))  (Sec. 4.2) */
+
+/* perturbation V_I(x), separable: sum over axes of v(x_d) */
+#define HFS_VI_NONE 0
+#define HFS_VI_X4 1  /* v(x) = x^4 */
+#define HFS_VI_COS 2 /* v(x) = cos(vi_k x) */
+
+/* splittings (Sec. 2.1) */
+#define HFS_SPLIT_HO 0      /* A = p^2/2mu + mu omega^2 x^2/2, B = eps V_I + sigma|psi|^2 (Eq. HermiteSplit) */
+#define HFS_SPLIT_FOURIER 1 /* A = p^2/2mu, B = mu omega^2 x^2/2 + eps V_I + sigma|psi|^2 (Eq. FourierSplit) */
+
+/* harmonic flow of one A stage under the HO split */
+#define HFS_FLOW_LEMMA2 0 /* exact flow for constant omega (Lemma 2) */
+#define HFS_FLOW_CF4 1    /* 4th-order commutator-free Magnus (Eq. CommutatorFree) + Theorem 2 */
+#define HFS_FLOW_M6 2     /* 6th-order Magnus (Sec. 4.2) + Theorem 1 */
+
+/* compositions (BAB form: m A-stages, m+1 B-stages; Eq. LeapFrogB, Table 1) */
+#define HFS_COMP_STRANG 0
+#define HFS_COMP_SRKN6_4 1
+#define HFS_COMP_NI4_82 2
+#define HFS_COMP_NI5_84 3
+#define HFS_COMP_CUSTOM 4
+
+/* execution modes of the 1D batched step */
+#define HFS_MODE_RESIDENT 0  /* every step of a call on-chip: one load + one store per instance */
+#define HFS_MODE_STREAMING 1 /* steps_per_launch steps per launch, one global round trip each */
+
+/* ---- problem description ----------------------------------------------- */
+typedef struct {
+    int32_t n[3];          /* grid points per axis (power of two); 1D uses n[0] */
+    double lo[3], hi[3];   /* periodic box [lo_d, hi_d) */
+    double mu;             /* mass (mu > 0) */
+    int32_t omega_law;     /* HFS_OMEGA_* */
+    double w0;             /* base frequency */
+    double law[3];         /* law parameters, see HFS_OMEGA_* */
+    double axis_scale[3];  /* 3D: omega_d = axis_scale[d] * omega(t); ignored in 1D */
+    double eps;            /* perturbation strength */
+    int32_t vi_kind;       /* HFS_VI_* */
+    double vi_k;           /* wavenumber for HFS_VI_COS */
+    double sigma;          /* nonlinearity (>0 repulsive, <0 attractive) */
+} hfs_instance;
+
+typedef struct hfs_ctx_s *hfs_ctx_t;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Create a context for `count` 1D instances (dim == 1; each n[0] in
+ * {128, ..., 4096}) or for one 3D instance (dim == 3, count == 1, n = 128^3
+ * or 32^3 / 64^3 per axis, all axes equal).  `inst` is a host array that is
+ * copied.  precision: HFS_C64 or HFS_C128.  Needs a current CUDA device.
+ * Errors: HFS_ERR_INVALID_ARG, HFS_ERR_UNSUPPORTED, HFS_ERR_CUDA. */
+int hfs_create(hfs_ctx_t *ctx, int dim, int precision, const hfs_instance *inst, int64_t count);
+
+/* Release the context (host memory only; caller-owned buffers untouched). */
+void hfs_destroy(hfs_ctx_t ctx);
+
+/* Stream for all later device work (a cudaStream_t, or NULL). */
+int hfs_set_stream(hfs_ctx_t ctx, void *cuda_stream);
+
+/* Total complex elements of the state and its size in bytes. */
+int hfs_state_size(hfs_ctx_t ctx, int64_t *elems, size_t *bytes);
+
+/* Element offset of instance i inside the state buffer. */
+int hfs_instance_offset(hfs_ctx_t ctx, int64_t i, int64_t *elem_offset);
+
+/* Workspace bytes needed when hfs_step() processes at most `chunk_steps`
+ * steps per schedule chunk (longer calls are split into chunks). */
+int hfs_workspace_size(hfs_ctx_t ctx, int64_t chunk_steps, size_t *bytes);
+
+/* Bind caller-owned device buffers: psi (state_size bytes) and a workspace
+ * of work_bytes (>= hfs_workspace_size for the chunk length given).  Both
+ * 256-byte aligned.  Initialises the workspace tables on the stream.
+ * Errors: HFS_ERR_INVALID_ARG, HFS_ERR_ALIGNMENT, HFS_ERR_WORKSPACE. */
+int hfs_bind(hfs_ctx_t ctx, void *psi_dev, void *work_dev, size_t work_bytes, int64_t chunk_steps);
+
+/* ---- schedule (Sec. 2, Table "algorithm"; Sec. 3) ---------------------- */
+
+/* Choose the splitting, the harmonic flow and the composition, and the time
+ * step dt (may be negative).  For HFS_COMP_CUSTOM pass a[na], b[nb] with
+ * nb == na + 1 (b_1 applied first); otherwise a/b may be NULL.  The
+ * validity |a_i dt| omega_max < pi is checked per instance at hfs_step().
+ * Errors: HFS_ERR_INVALID_ARG. */
+int hfs_set_schedule(hfs_ctx_t ctx, int split, int ho_flow, int composition, const double *a, int na,
+                     const double *b, int nb, double dt);
+
+/* Execution mode of the 1D step (default HFS_MODE_RESIDENT) and, for
+ * HFS_MODE_STREAMING, the number of steps fused per launch (>= 1). */
+int hfs_set_mode(hfs_ctx_t ctx, int mode, int steps_per_launch);
+
+/* Capture each hfs_step(nsteps) launch sequence in a CUDA graph and replay
+ * it on later calls with the same nsteps (enable != 0).  Capture needs a
+ * stream other than the legacy default stream: hfs_step() returns
+ * HFS_ERR_INVALID_ARG when graphs are enabled and the stream is NULL. */
+int hfs_set_graphs(hfs_ctx_t ctx, int enable);
+
+/* Current time t_n (host copy; advanced by hfs_step). */
+int hfs_set_time(hfs_ctx_t ctx, double t);
+int hfs_get_time(hfs_ctx_t ctx, double *t);
+
+/* ---- state ------------------------------------------------------------- */
+
+/* Copy a full state (state_size bytes) into / out of the bound psi buffer.
+ * on_device != 0: src/dst is device memory, else host memory. */
+int hfs_set_psi(hfs_ctx_t ctx, const void *src, int src_on_device);
+int hfs_get_psi(hfs_ctx_t ctx, void *dst, int dst_on_device);
+
+/* Advance every instance by nsteps steps of the schedule from the current
+ * time (asynchronous).  Errors: HFS_ERR_NOT_READY, HFS_ERR_STEP_TOO_LARGE,
+ * HFS_ERR_CUDA. */
+int hfs_step(hfs_ctx_t ctx, int64_t nsteps);
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+/* Discrete norm dV sum_j |psi_j|^2 per instance (FP64 accumulation), into
+ * the host array out[count]. */
+int hfs_norm(hfs_ctx_t ctx, double *out);
+
+/* Energy per instance at the current time:
+ * dV sum_j [ |grad psi|^2/(2 mu) + V(x_j,t)|psi_j|^2 + sigma/2 |psi_j|^4 ],
+ * V = mu omega^2(t) x^2 / 2 + eps V_I; gradient spectral.  Host out[count]. */
+int hfs_energy(hfs_ctx_t ctx, double *out);
+
+/* Wait for the stream, then read and clear the device status word. */
+int hfs_sync_status(hfs_ctx_t ctx);
+
+/* ---- plans / autotuning (1D) ------------------------------------------- */
+
+/* Set the plan for grid size n: elements per thread (8 or 16).  Affects
+ * later hfs_step calls.  Errors: HFS_ERR_UNSUPPORTED. */
+int hfs_set_plan(hfs_ctx_t ctx, int n, int elems_per_thread);
+
+/* Time each supported plan for each grid size present in the batch with
+ * CUDA events (trial_steps steps, resident mode) and keep the fastest.
+ * Overwrites the state: call before hfs_set_psi.  best_ept[6] (host, may be
+ * NULL) receives the chosen elements-per-thread for n = 128 ... 4096 (0 when
+ * the size is absent). */
+int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_ept);
+
+const char *hfs_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,737 @@
+// hfs_api.cu -- the C ABI of include/hfs.h: contexts, caller-owned buffer
+// binding, host-side validation, chunked schedule + step launches, CUDA
+// graph capture, diagnostics and the 1D plan autotuner.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "hfs.h"
+#include "hfs_internal.cuh"
+#include "hfs_sched.h"
+#include "hfs_step3d.h"
+
+using namespace hfs;
+
+namespace {
+
+struct Layout {
+    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, rec, diag, total;
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct hfs_ctx_s {
+    int dim = 1, precision = HFS_C64;
+    int64_t count = 0;
+    std::vector<hfs_instance> inst;
+    std::vector<DevInst> dinst;
+    std::vector<int64_t> offsets;
+    int64_t elems = 0;
+    // 1D plans: elements per thread per size class
+    int ept[kNumSizes] = {16, 16, 16, 16, 16, 16};
+    std::vector<int32_t> order;  // sorted position -> instance
+    std::vector<WorkItem> work;
+    // schedule
+    bool have_sched = false;
+    SchedConst sc{};
+    int composition = HFS_COMP_STRANG;
+    // execution
+    int mode = HFS_MODE_RESIDENT, spl = 1;
+    bool graphs = false;
+    cudaStream_t stream = nullptr;
+    // bound buffers
+    void *psi = nullptr;
+    unsigned char *work_base = nullptr;
+    size_t work_bytes = 0;
+    int64_t chunk = 0;
+    Layout lay{};
+    double t = 0.0;
+    int sm_count = 0;
+    // graph cache keyed by nsteps
+    std::map<int64_t, cudaGraphExec_t> graphs_by_n;
+    uint64_t version = 0;  // bumps invalidate cached graphs
+    std::vector<double> diag_host;
+};
+
+namespace {
+
+#define CK(expr)                                                                                                  \
+    do {                                                                                                          \
+        cudaError_t _e = (expr);                                                                                  \
+        if (_e != cudaSuccess) return HFS_ERR_CUDA;                                                               \
+    } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int composition_coeffs(int comp, std::vector<double> &a, std::vector<double> &b)
+{
+    // BAB compositions, b_1 applied first (Eq. LeapFrogB; Table 1)
+    switch (comp) {
+    case HFS_COMP_STRANG:
+        a = {1.0};
+        b = {0.5, 0.5};
+        return 0;
+    case HFS_COMP_SRKN6_4: {
+        const double b1 = 0.0829844064174052, b2 = 0.396309801498368, b3 = -0.0390563049223486;
+        const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
+        const double a1 = 0.245298957184271, a2 = 0.604872665711080, a3 = 0.5 - (a1 + a2);
+        a = {a1, a2, a3, a3, a2, a1};
+        b = {b1, b2, b3, b4, b3, b2, b1};
+        return 0;
+    }
+    case HFS_COMP_NI4_82: {
+        // Table 1 prints b_2 = 49/18; the (8,2) method's weights are the
+        // Lobatto weights 1/20, 49/180, 16/45, so b_2 = 49/180.
+        const double b1 = 1.0 / 20.0, b2 = 49.0 / 180.0, b3 = 1.0 - 2.0 * (b1 + b2);
+        const double a1 = 0.5 - sqrt(3.0 / 28.0), a2 = 0.5 - a1;
+        a = {a1, a2, a2, a1};
+        b = {b1, b2, b3, b2, b1};
+        return 0;
+    }
+    case HFS_COMP_NI5_84: {
+        const double b1 = 0.811862738544516, b2 = -0.677480399532169, b3 = 0.5 - (b1 + b2);
+        const double a1 = -0.00758691311877447, a2 = 0.317218277973169, a3 = 1.0 - 2.0 * (a1 + a2);
+        a = {a1, a2, a3, a2, a1};
+        b = {b1, b2, b3, b3, b2, b1};
+        return 0;
+    }
+    default:
+        return -1;
+    }
+}
+
+// upper bound of omega over [t0, t1] for the validity check
+double omega_bound(const hfs_instance &p, double t0, double t1)
+{
+    const double aw = fabs(p.w0);
+    switch (p.omega_law) {
+    case HFS_OMEGA_CONST:
+        return aw;
+    case HFS_OMEGA_SIN:
+        return aw * (1.0 + fabs(p.law[0]));
+    case HFS_OMEGA_COS_SQ:
+        return aw * sqrt(1.0 + fabs(p.law[0]));
+    case HFS_OMEGA_PULSE:
+        return aw * (1.0 + fabs(p.law[0]) * std::max(fabs(t0), fabs(t1)));
+    default:
+        return INFINITY;
+    }
+}
+
+Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    const int m = std::max(c->have_sched ? c->sc.m : 0, 6);
+    const int64_t nstage = chunk * m;
+    const size_t recsz = (c->dim == 1) ? (c->precision == HFS_C128 ? sizeof(RecD) : sizeof(RecF))
+                                       : (c->precision == HFS_C128 ? sizeof(Rec3D) : sizeof(Rec3F));
+    L.status = take(sizeof(unsigned));
+    L.ticket = take(sizeof(unsigned));
+    L.tdev = take(sizeof(double));
+    L.inst = take(sizeof(DevInst) * c->count);
+    L.order = take(sizeof(int32_t) * c->count);
+    L.work = take(sizeof(WorkItem) * std::max<int64_t>(c->count, 1));
+    L.twf = take(sizeof(float4) * kTwiddleTotal);
+    L.twd = take(sizeof(cpx<double>) * kTwiddleTotal);
+    L.fge = take(sizeof(StageFGE) * c->count * nstage * c->dim);
+    L.rec = take(recsz * c->count * (nstage + 1));
+    L.diag = take(sizeof(double) * 2 * std::max<int64_t>(c->count, 1));
+    L.total = o;
+    return L;
+}
+
+template <typename T> T *wptr(hfs_ctx_s *c, size_t off) { return reinterpret_cast<T *>(c->work_base + off); }
+
+void build_worklist(hfs_ctx_s *c)
+{
+    c->order.resize(c->count);
+    std::iota(c->order.begin(), c->order.end(), 0);
+    std::stable_sort(c->order.begin(), c->order.end(),
+                     [&](int32_t x, int32_t y) { return c->inst[x].n[0] > c->inst[y].n[0]; });
+    c->work.clear();
+    int64_t i = 0;
+    while (i < c->count) {
+        const int n = c->inst[c->order[i]].n[0];
+        const int e = c->ept[size_class(n)];
+        const int per = kCtaThreads / (n / e);
+        int64_t j = i;
+        while (j < c->count && j - i < per && c->inst[c->order[j]].n[0] == n) ++j;
+        WorkItem w;
+        w.first = (int32_t)i;
+        w.count = (int32_t)(j - i);
+        w.plan = plan_id(n, e);
+        w.pad = 0;
+        c->work.push_back(w);
+        i = j;
+    }
+}
+
+int upload_tables(hfs_ctx_s *c)
+{
+    CK(cudaMemcpyAsync(wptr<void>(c, c->lay.order), c->order.data(), sizeof(int32_t) * c->count,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(wptr<void>(c, c->lay.work), c->work.data(), sizeof(WorkItem) * c->work.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    return HFS_OK;
+}
+
+void drop_graphs(hfs_ctx_s *c)
+{
+    for (auto &kv : c->graphs_by_n) cudaGraphExecDestroy(kv.second);
+    c->graphs_by_n.clear();
+    c->version++;
+}
+
+int check_validity(const hfs_ctx_s *c, int64_t nsteps)
+{
+    if (c->sc.split != HFS_SPLIT_HO) return HFS_OK;
+    double amax = 0.0;
+    for (int i = 0; i < c->sc.m; ++i) amax = std::max(amax, fabs(c->sc.a[i] * c->sc.h));
+    const double t0 = c->t, t1 = c->t + (double)nsteps * c->sc.h;
+    for (int64_t i = 0; i < c->count; ++i) {
+        const hfs_instance &p = c->inst[i];
+        double scale = 1.0;
+        if (c->dim == 3) scale = std::max({fabs(p.axis_scale[0]), fabs(p.axis_scale[1]), fabs(p.axis_scale[2])});
+        const double om = omega_bound(p, t0, t1) * scale;
+        if (!(amax * om < M_PI)) return HFS_ERR_STEP_TOO_LARGE;
+    }
+    return HFS_OK;
+}
+
+// enqueue nsteps steps (no graph logic); work list already uploaded
+int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
+{
+    (void)cudaGetLastError();  // a failed earlier runtime call must not be reported by the launches below
+    const bool fp64 = c->precision == HFS_C128;
+    const int m = c->sc.m;
+    unsigned *status = wptr<unsigned>(c, c->lay.status);
+    unsigned *ticket = wptr<unsigned>(c, c->lay.ticket);
+    double *tdev = wptr<double>(c, c->lay.tdev);
+    const DevInst *dinst = wptr<DevInst>(c, c->lay.inst);
+    StageFGE *fge = wptr<StageFGE>(c, c->lay.fge);
+    void *rec = wptr<void>(c, c->lay.rec);
+    int64_t done = 0;
+    while (done < nsteps) {
+        const int64_t S = std::min(c->chunk, nsteps - done);
+        const int64_t nstage = S * m;
+        const double toff = (double)done * c->sc.h;
+        if (c->sc.split == HFS_SPLIT_HO)
+            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, fge, status, c->stream));
+        if (c->dim == 1) {
+            CK(launch_records1d(fp64, dinst, c->count, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
+            Step1DArgs a{};
+            a.psi = c->psi;
+            a.inst = dinst;
+            a.order = wptr<int32_t>(c, c->lay.order);
+            a.work = wptr<WorkItem>(c, c->lay.work);
+            a.nwork = (int32_t)c->work.size();
+            a.rec = rec;
+            a.nrec = nstage + 1;
+            a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
+            a.ticket = ticket;
+            a.status = status;
+            const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64)));
+            const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
+            for (int64_t s0 = 0; s0 < S; s0 += per) {
+                const int64_t s1 = std::min(S, s0 + per);
+                a.j0 = s0 * m;
+                a.j1 = s1 * m;
+                a.final_x = (s1 == S) ? 1 : 0;
+                CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
+                CK(launch_step1d(fp64, a, grid, c->stream));
+            }
+        } else {
+            CK(launch_records3d(fp64, dinst, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
+            Step3DArgs a{};
+            a.psi = c->psi;
+            a.inst = dinst;
+            a.rec = rec;
+            a.nstage = nstage;
+            a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
+            a.status = status;
+            a.n = c->inst[0].n[0];
+            CK(launch_step3d(fp64, a, c->stream));
+        }
+        done += S;
+    }
+    CK(launch_advance_time(tdev, (double)nsteps * c->sc.h, c->stream));
+    return HFS_OK;
+}
+
+int ready(const hfs_ctx_s *c)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    if (!c->psi || !c->work_base) return HFS_ERR_NOT_READY;
+    return HFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hfs_error_string(int s)
+{
+    switch (s) {
+    case HFS_OK: return "ok";
+    case HFS_ERR_INVALID_ARG: return "invalid argument";
+    case HFS_ERR_UNSUPPORTED: return "unsupported grid size, dimension or precision";
+    case HFS_ERR_STEP_TOO_LARGE: return "time step outside the validity of the chirp-kinetic-chirp decomposition";
+    case HFS_ERR_CUDA: return "CUDA runtime error";
+    case HFS_ERR_NONFINITE: return "non-finite value detected";
+    case HFS_ERR_NOT_READY: return "buffers not bound or schedule not set";
+    case HFS_ERR_ALIGNMENT: return "buffer not 256-byte aligned";
+    case HFS_ERR_WORKSPACE: return "workspace too small";
+    case HFS_ERR_DEVICE_TIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+    }
+}
+
+int hfs_create(hfs_ctx_t *out, int dim, int precision, const hfs_instance *inst, int64_t count)
+{
+    if (!out || !inst || count <= 0) return HFS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (precision != HFS_C64 && precision != HFS_C128) return HFS_ERR_INVALID_ARG;
+    if (dim != 1 && dim != 3) return HFS_ERR_UNSUPPORTED;
+    if (dim == 3 && count != 1) return HFS_ERR_UNSUPPORTED;
+    if (count > (int64_t)1 << 30) return HFS_ERR_INVALID_ARG;
+    hfs_ctx_s *c = new (std::nothrow) hfs_ctx_s();
+    if (!c) return HFS_ERR_INVALID_ARG;
+    c->dim = dim;
+    c->precision = precision;
+    c->count = count;
+    c->inst.assign(inst, inst + count);
+    c->dinst.resize(count);
+    c->offsets.resize(count);
+    int64_t off = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const hfs_instance &p = inst[i];
+        DevInst &d = c->dinst[i];
+        memset(&d, 0, sizeof(d));
+        if (!(p.mu > 0.0) || p.omega_law < 0 || p.omega_law > 3 || p.vi_kind < 0 || p.vi_kind > 2) {
+            delete c;
+            return HFS_ERR_INVALID_ARG;
+        }
+        int64_t pts = 1;
+        for (int a = 0; a < dim; ++a) {
+            const int n = p.n[a];
+            if (!is_pow2(n)) {
+                delete c;
+                return HFS_ERR_UNSUPPORTED;
+            }
+            if (dim == 1 && (n < 128 || n > 4096)) {
+                delete c;
+                return HFS_ERR_UNSUPPORTED;
+            }
+            if (!(p.hi[a] > p.lo[a])) {
+                delete c;
+                return HFS_ERR_INVALID_ARG;
+            }
+            d.n[a] = n;
+            d.len[a] = p.hi[a] - p.lo[a];
+            d.dx[a] = d.len[a] / n;
+            d.xc[a] = 0.5 * (p.lo[a] + p.hi[a]);
+            pts *= n;
+        }
+        if (dim == 3) {
+            if (!step3d_supported(p.n[0], p.n[1], p.n[2]) || d.xc[0] != 0.0 || d.xc[1] != 0.0 || d.xc[2] != 0.0) {
+                delete c;
+                return HFS_ERR_UNSUPPORTED;
+            }
+        }
+        d.off = off;
+        c->offsets[i] = off;
+        off += pts;
+        d.mu = p.mu;
+        d.omega_law = p.omega_law;
+        d.vi_kind = p.vi_kind;
+        d.w0 = p.w0;
+        for (int a = 0; a < 3; ++a) {
+            d.law[a] = p.law[a];
+            d.axis_scale[a] = (dim == 3) ? p.axis_scale[a] : 1.0;
+        }
+        d.eps = p.eps;
+        d.vi_k = p.vi_k;
+        d.sigma = p.sigma;
+        d.plan = (dim == 1) ? size_class(p.n[0]) : 0;
+    }
+    c->elems = off;
+    if (dim == 1) build_worklist(c);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete c;
+        return HFS_ERR_CUDA;
+    }
+    c->diag_host.resize(2 * count);
+    *out = c;
+    return HFS_OK;
+}
+
+void hfs_destroy(hfs_ctx_t c)
+{
+    if (!c) return;
+    drop_graphs(c);
+    delete c;
+}
+
+int hfs_set_stream(hfs_ctx_t c, void *stream)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    if (c->stream != (cudaStream_t)stream) drop_graphs(c);
+    c->stream = (cudaStream_t)stream;
+    return HFS_OK;
+}
+
+int hfs_state_size(hfs_ctx_t c, int64_t *elems, size_t *bytes)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    const size_t es = (c->precision == HFS_C128) ? 16 : 8;
+    if (elems) *elems = c->elems;
+    if (bytes) *bytes = (size_t)c->elems * es;
+    return HFS_OK;
+}
+
+int hfs_instance_offset(hfs_ctx_t c, int64_t i, int64_t *off)
+{
+    if (!c || !off || i < 0 || i >= c->count) return HFS_ERR_INVALID_ARG;
+    *off = c->offsets[i];
+    return HFS_OK;
+}
+
+int hfs_workspace_size(hfs_ctx_t c, int64_t chunk_steps, size_t *bytes)
+{
+    if (!c || !bytes || chunk_steps <= 0) return HFS_ERR_INVALID_ARG;
+    *bytes = make_layout(c, chunk_steps).total;
+    return HFS_OK;
+}
+
+int hfs_bind(hfs_ctx_t c, void *psi, void *work, size_t work_bytes, int64_t chunk_steps)
+{
+    if (!c || !psi || !work || chunk_steps <= 0) return HFS_ERR_INVALID_ARG;
+    if (((uintptr_t)psi & 255) || ((uintptr_t)work & 255)) return HFS_ERR_ALIGNMENT;
+    const Layout L = make_layout(c, chunk_steps);
+    if (work_bytes < L.total) return HFS_ERR_WORKSPACE;
+    drop_graphs(c);
+    c->psi = psi;
+    c->work_base = (unsigned char *)work;
+    c->work_bytes = work_bytes;
+    c->chunk = chunk_steps;
+    c->lay = L;
+    (void)cudaGetLastError();
+    CK(cudaMemsetAsync(wptr<void>(c, L.status), 0, sizeof(unsigned), c->stream));
+    CK(cudaMemcpyAsync(wptr<void>(c, L.inst), c->dinst.data(), sizeof(DevInst) * c->count, cudaMemcpyHostToDevice,
+                       c->stream));
+    if (c->dim == 1) {
+        int s = upload_tables(c);
+        if (s) return s;
+    }
+    CK(launch_twiddles(wptr<void>(c, L.twf), wptr<void>(c, L.twd), c->stream));
+    CK(launch_set_time(wptr<double>(c, L.tdev), c->t, c->stream));
+    return HFS_OK;
+}
+
+int hfs_set_schedule(hfs_ctx_t c, int split, int ho_flow, int composition, const double *a, int na,
+                     const double *b, int nb, double dt)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    if (split != HFS_SPLIT_HO && split != HFS_SPLIT_FOURIER) return HFS_ERR_INVALID_ARG;
+    if (ho_flow < HFS_FLOW_LEMMA2 || ho_flow > HFS_FLOW_M6) return HFS_ERR_INVALID_ARG;
+    if (!(dt != 0.0) || !isfinite(dt)) return HFS_ERR_INVALID_ARG;
+    std::vector<double> av, bv;
+    if (composition == HFS_COMP_CUSTOM) {
+        if (!a || !b || na < 1 || na > kMaxStages || nb != na + 1) return HFS_ERR_INVALID_ARG;
+        av.assign(a, a + na);
+        bv.assign(b, b + nb);
+    } else if (composition_coeffs(composition, av, bv)) {
+        return HFS_ERR_INVALID_ARG;
+    }
+    SchedConst sc{};
+    sc.split = split;
+    sc.flow = ho_flow;
+    sc.m = (int)av.size();
+    sc.h = dt;
+    double cum = 0.0;
+    for (int i = 0; i < sc.m; ++i) {
+        sc.a[i] = av[i];
+        sc.cuma[i] = cum;
+        cum += av[i];
+    }
+    for (int i = 0; i <= sc.m; ++i) sc.b[i] = bv[i];
+    if (c->work_base) {
+        // the bound workspace must hold this schedule's chunk
+        hfs_ctx_s probe = {};
+        probe.dim = c->dim;
+        probe.precision = c->precision;
+        probe.count = c->count;
+        probe.have_sched = true;
+        probe.sc = sc;
+        if (make_layout(&probe, c->chunk).total > c->work_bytes) return HFS_ERR_WORKSPACE;
+        c->lay = make_layout(&probe, c->chunk);
+    }
+    c->sc = sc;
+    c->have_sched = true;
+    c->composition = composition;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+int hfs_set_mode(hfs_ctx_t c, int mode, int spl)
+{
+    if (!c || (mode != HFS_MODE_RESIDENT && mode != HFS_MODE_STREAMING) || spl < 1) return HFS_ERR_INVALID_ARG;
+    c->mode = mode;
+    c->spl = spl;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+int hfs_set_graphs(hfs_ctx_t c, int enable)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    c->graphs = enable != 0;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+int hfs_set_time(hfs_ctx_t c, double t)
+{
+    if (!c || !isfinite(t)) return HFS_ERR_INVALID_ARG;
+    c->t = t;
+    if (c->work_base) CK(launch_set_time(wptr<double>(c, c->lay.tdev), t, c->stream));
+    return HFS_OK;
+}
+
+int hfs_get_time(hfs_ctx_t c, double *t)
+{
+    if (!c || !t) return HFS_ERR_INVALID_ARG;
+    *t = c->t;
+    return HFS_OK;
+}
+
+int hfs_set_psi(hfs_ctx_t c, const void *src, int on_device)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!src) return HFS_ERR_INVALID_ARG;
+    size_t bytes = 0;
+    hfs_state_size(c, nullptr, &bytes);
+    CK(cudaMemcpyAsync(c->psi, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return HFS_OK;
+}
+
+int hfs_get_psi(hfs_ctx_t c, void *dst, int on_device)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!dst) return HFS_ERR_INVALID_ARG;
+    size_t bytes = 0;
+    hfs_state_size(c, nullptr, &bytes);
+    CK(cudaMemcpyAsync(dst, c->psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return HFS_OK;
+}
+
+int hfs_step(hfs_ctx_t c, int64_t nsteps)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!c->have_sched) return HFS_ERR_NOT_READY;
+    if (nsteps < 0) return HFS_ERR_INVALID_ARG;
+    if (nsteps == 0) return HFS_OK;
+    if (make_layout(c, c->chunk).total > c->work_bytes) return HFS_ERR_WORKSPACE;
+    s = check_validity(c, nsteps);
+    if (s) return s;
+    if (c->graphs) {
+        if (c->stream == nullptr) return HFS_ERR_INVALID_ARG;  // the legacy stream cannot be captured
+        auto it = c->graphs_by_n.find(nsteps);
+        if (it == c->graphs_by_n.end()) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            s = enqueue_steps(c, nsteps);
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (s) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            CK(e);
+            cudaGraphExec_t ge = nullptr;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            it = c->graphs_by_n.emplace(nsteps, ge).first;
+        }
+        CK(cudaGraphLaunch(it->second, c->stream));
+    } else {
+        s = enqueue_steps(c, nsteps);
+        if (s) return s;
+    }
+    c->t += (double)nsteps * c->sc.h;
+    return HFS_OK;
+}
+
+static int run_diag(hfs_ctx_s *c)
+{
+    (void)cudaGetLastError();
+    const bool fp64 = c->precision == HFS_C128;
+    double *dout = wptr<double>(c, c->lay.diag);
+    if (c->dim == 1) {
+        Diag1DArgs a{};
+        a.psi = c->psi;
+        a.inst = wptr<DevInst>(c, c->lay.inst);
+        a.order = wptr<int32_t>(c, c->lay.order);
+        a.work = wptr<WorkItem>(c, c->lay.work);
+        a.nwork = (int32_t)c->work.size();
+        a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
+        a.t_dev = wptr<double>(c, c->lay.tdev);
+        a.out = dout;
+        a.ticket = wptr<unsigned>(c, c->lay.ticket);
+        CK(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), c->stream));
+        const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64)));
+        CK(launch_diag1d(fp64, a, grid, c->stream));
+    } else {
+        Diag3DArgs a{};
+        a.psi = c->psi;
+        a.inst = wptr<DevInst>(c, c->lay.inst);
+        a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
+        a.t_dev = wptr<double>(c, c->lay.tdev);
+        a.out = dout;
+        a.n = c->inst[0].n[0];
+        CK(launch_diag3d(fp64, a, c->stream));
+    }
+    CK(cudaMemcpyAsync(c->diag_host.data(), dout, sizeof(double) * 2 * c->count, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HFS_OK;
+}
+
+int hfs_norm(hfs_ctx_t c, double *out)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!out) return HFS_ERR_INVALID_ARG;
+    s = run_diag(c);
+    if (s) return s;
+    for (int64_t i = 0; i < c->count; ++i) out[i] = c->diag_host[2 * i];
+    return HFS_OK;
+}
+
+int hfs_energy(hfs_ctx_t c, double *out)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!out) return HFS_ERR_INVALID_ARG;
+    s = run_diag(c);
+    if (s) return s;
+    for (int64_t i = 0; i < c->count; ++i) out[i] = c->diag_host[2 * i + 1];
+    return HFS_OK;
+}
+
+int hfs_sync_status(hfs_ctx_t c)
+{
+    int s = ready(c);
+    if (s) return s;
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, wptr<unsigned>(c, c->lay.status), sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(wptr<unsigned>(c, c->lay.status), 0, sizeof(unsigned), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st & ST_TIMEOUT) return HFS_ERR_DEVICE_TIMEOUT;
+    if (st & ST_NONFINITE) return HFS_ERR_NONFINITE;
+    if (st & ST_BADPLAN) return HFS_ERR_UNSUPPORTED;
+    return HFS_OK;
+}
+
+int hfs_set_plan(hfs_ctx_t c, int n, int ept)
+{
+    if (!c || c->dim != 1) return HFS_ERR_INVALID_ARG;
+    const int sc = size_class(n);
+    if (sc < 0 || (ept != 16 && ept != 8) || (ept == 8 && n > 2048)) return HFS_ERR_UNSUPPORTED;
+    c->ept[sc] = ept;
+    build_worklist(c);
+    drop_graphs(c);
+    if (c->work_base) return upload_tables(c);
+    return HFS_OK;
+}
+
+int hfs_autotune(hfs_ctx_t c, int trial_steps, int32_t *best_ept)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!c->have_sched || c->dim != 1 || trial_steps < 1) return HFS_ERR_INVALID_ARG;
+    const int64_t steps = std::min<int64_t>(trial_steps, c->chunk);
+    std::vector<hfs_instance> all = c->inst;
+    bool present[kNumSizes] = {};
+    for (auto &p : all) present[size_class(p.n[0])] = true;
+    // fill psi with a smooth constant so that the trial is well defined
+    size_t bytes = 0;
+    hfs_state_size(c, nullptr, &bytes);
+    CK(cudaMemsetAsync(c->psi, 0, bytes, c->stream));
+    const bool graphs = c->graphs;
+    c->graphs = false;
+    const double t_save = c->t;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int options[2] = {16, 8};
+    for (int k = 0; k < kNumSizes; ++k) {
+        if (!present[k]) {
+            if (best_ept) best_ept[k] = 0;
+            continue;
+        }
+        const int n = 128 << k;
+        float best = INFINITY;
+        int best_e = c->ept[k];
+        for (int oi = 0; oi < 2; ++oi) {
+            const int e = options[oi];
+            if (e == 8 && n > 2048) continue;
+            // restrict the work list to this size class
+            c->ept[k] = e;
+            build_worklist(c);
+            std::vector<WorkItem> keep;
+            for (auto &w : c->work)
+                if (w.plan == plan_id(n, e)) keep.push_back(w);
+            c->work.swap(keep);
+            s = upload_tables(c);
+            if (s) break;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+                CK(cudaEventRecord(e0, c->stream));
+                s = enqueue_steps(c, steps);
+                if (s) break;
+                CK(cudaEventRecord(e1, c->stream));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (s) break;
+            if (ms < best) {
+                best = ms;
+                best_e = e;
+            }
+        }
+        if (s) break;
+        c->ept[k] = best_e;
+        if (best_ept) best_ept[k] = best_e;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->graphs = graphs;
+    build_worklist(c);
+    int s2 = upload_tables(c);
+    c->t = t_save;
+    if (c->work_base) CK(launch_set_time(wptr<double>(c, c->lay.tdev), t_save, c->stream));
+    drop_graphs(c);
+    return s ? s : s2;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// hfs_internal.cuh -- device data layouts shared by the library's kernels
+// and its host code (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hfs.h"
+
+namespace hfs {
+
+// ---------------------------------------------------------------------------
+// complex values: interleaved (re, im), 8- or 16-byte aligned
+// ---------------------------------------------------------------------------
+template <typename R> struct alignas(2 * sizeof(R)) cpx {
+    R x, y;
+};
+
+template <typename R> __device__ __forceinline__ cpx<R> cadd(cpx<R> a, cpx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R> __device__ __forceinline__ cpx<R> csub(cpx<R> a, cpx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R> __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename R> __device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b)
+{
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+
+// ---------------------------------------------------------------------------
+// per-instance parameters as the kernels see them
+// ---------------------------------------------------------------------------
+struct DevInst {
+    int64_t off;          // element offset of the instance in psi
+    int32_t n[3];         // points per axis
+    int32_t plan;         // 1D: index into the plan table (grid size class)
+    double xc[3];         // box centre per axis, x_j = xc + (j - n/2) dx
+    double dx[3];         // mesh width per axis
+    double len[3];        // box length per axis
+    double mu;
+    int32_t omega_law;
+    int32_t vi_kind;
+    double w0;
+    double law[3];
+    double axis_scale[3];
+    double eps, vi_k, sigma;
+};
+
+// FSAL-merged record of sub-stage j (FP32 path, 32 bytes):
+//   x-phase X_j :  turns(x) = K2 m^2 + K1 m + K0   with m = j - n/2
+//                  plus sB2pi * (eps V_I(x) + sigma |u|^2)   [+ F-split trap]
+//   drift D_{j+1}: turns(k) = G m_k^2             with m_k the signed wavenumber index
+// Every "turns" coefficient is carried as an unevaluated float sum hi + lo.
+struct alignas(16) RecF {
+    float k2hi, k2lo, k1hi, k1lo;
+    float k0, sb2pi, ghi, glo;
+};
+// FP64 path (48 bytes)
+struct alignas(16) RecD {
+    double k2, k1, k0, sb2pi, g, pad;
+};
+
+// per-stage harmonic-flow coefficients (FP64), one record per axis
+struct alignas(16) StageFGE {
+    double f, g, e, tau;
+};
+
+// device status word bits
+enum : unsigned {
+    ST_NONFINITE = 1u,
+    ST_TIMEOUT = 2u,
+    ST_BADPLAN = 4u,
+};
+
+// 1D work item: `count` consecutive instances (after sorting) of one plan
+struct WorkItem {
+    int32_t first;  // index into the sorted instance order
+    int32_t count;  // instances in this item (<= instances per CTA)
+    int32_t plan;   // plan id (grid size class + elements per thread)
+    int32_t pad;
+};
+
+// supported 1D sizes
+constexpr int kNumSizes = 6;  // 128 ... 4096
+__host__ __device__ constexpr int size_class(int n)
+{
+    return n == 128 ? 0 : n == 256 ? 1 : n == 512 ? 2 : n == 1024 ? 3 : n == 2048 ? 4 : n == 4096 ? 5 : -1;
+}
+// plan id = size_class * 2 + (ept == 8 ? 1 : 0)
+__host__ __device__ constexpr int plan_id(int n, int ept) { return size_class(n) * 2 + (ept == 8 ? 1 : 0); }
+
+constexpr int kCtaThreads = 256;
+
+// twiddle table: concatenation of exp(-2 pi i k / n), k < n, for n = 16..4096
+// (powers of two); the table of size n starts at 16 + 32 + ... + n/2 = n - 16
+__host__ __device__ constexpr int64_t twiddle_offset(int n) { return n - 16; }
+constexpr int64_t kTwiddleTotal = 8192 - 16;
+
+}  // namespace hfs

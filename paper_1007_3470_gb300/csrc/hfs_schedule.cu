@@ -1,0 +1,311 @@
+// hfs_schedule.cu -- device-side FP64 schedule of the Magnus and
+// decomposition coefficients.
+//
+// Kernel 1 (stage_flow_kernel): for every instance, stage and axis, the
+// harmonic flow of one A stage over [tau, tau + a_i h] as kick(f) .
+// drift(g) . kick(e), e applied first:
+//   * exact flow for constant omega (Lemma 2 with mu, omega):
+//       g = sin(omega s)/(mu omega), f = e = mu omega tan(omega s/2);
+//   * commutator-free Magnus-4 (Eq. CommutatorFree): two half steps with
+//       omega_L^2 = al w1 + be w2, omega_R^2 = be w1 + al w2 (R first),
+//       w_k = omega^2(tau + c_k s), c = 1/2 -+ sqrt(3)/6, al = 1/2 - 1/sqrt3,
+//     decomposed by Theorem 2;
+//   * sixth-order Magnus (Sec. 4.2), omega^2 read at the three Gauss nodes,
+//     decomposed by Theorem 1.
+// The trigonometric quantities are written in the forms C(w,t)=cos(sqrt(w)t)
+// and S(w,t)=sin(sqrt(w)t)/sqrt(w), continued to w <= 0, with
+// 1 - cos = 2 sin^2(half angle), so that no difference of nearly equal
+// numbers is formed for small steps.
+//
+// Kernel 2 (records kernels): merges adjacent chirps and B flows as in
+// Eq. prod-genHarmOsc -- the kick between drifts i and i+1 is f_i + e_{i+1}
+// and the B flows at a step boundary add (b_{m+1} + b_1) h (FSAL) -- and
+// converts every coefficient into phase "turns" per unit integer index:
+//   kick   kappa x^2/2 / (2 pi),   x = xc + m dx
+//          -> K2 = kappa dx^2/(4 pi), K1 = kappa xc dx/(2 pi), K0 = kappa xc^2/(4 pi) mod 1
+//   drift  g k^2/2 / (2 pi),       k = 2 pi m_k / L  ->  G = g pi / L^2
+//   B      s (eps V_I + sigma |u|^2) / (2 pi)       ->  sb2pi = s / (2 pi)
+// For the F split (Eq. FourierSplit) the drift is g = a_i h / mu and the
+// trap mu omega^2(tau) x^2/2 of every B flow joins the kick at its frozen
+// time.
+#include <math.h>
+
+#include "hfs_internal.cuh"
+#include "hfs_law.cuh"
+#include "hfs_sched.h"
+
+namespace hfs {
+
+// C = cos(sqrt(w) t), S = sin(sqrt(w) t)/sqrt(w), OMC = 1 - C, continued to w <= 0
+struct CS {
+    double C, S, OMC;
+};
+__device__ CS cs_of(double w, double t)
+{
+    CS r;
+    if (w > 0.0) {
+        const double q = sqrt(w);
+        double sh, ch;
+        sincos(0.5 * q * t, &sh, &ch);
+        r.C = 1.0 - 2.0 * sh * sh;
+        r.OMC = 2.0 * sh * sh;
+        r.S = 2.0 * sh * ch / q;
+    } else if (w < 0.0) {
+        const double q = sqrt(-w);
+        const double sh = sinh(0.5 * q * t), ch = cosh(0.5 * q * t);
+        r.C = 1.0 + 2.0 * sh * sh;
+        r.OMC = -2.0 * sh * sh;
+        r.S = 2.0 * sh * ch / q;
+    } else {
+        r.C = 1.0;
+        r.OMC = 0.0;
+        r.S = t;
+    }
+    return r;
+}
+
+// Theorem 2 for the product of two half steps (R applied first), mu = 1
+__device__ void fge_thm2(double wl, double wr, double s, double &f, double &g, double &e)
+{
+    const CS L = cs_of(wl, 0.5 * s), Rr = cs_of(wr, 0.5 * s);
+    g = L.S * Rr.C + L.C * Rr.S;
+    const double omcc = L.OMC + L.C * Rr.OMC;  // 1 - C_L C_R
+    const double ss = L.S * Rr.S;
+    f = (omcc + wl * ss) / g;
+    e = (omcc + wr * ss) / g;
+}
+
+// Theorem 1 for exp(-i s/2 (al x^2 + be (xp+px) + ga p^2))
+__device__ void fge_thm1(double al, double be, double ga, double s, double &f, double &g, double &e)
+{
+    const CS r = cs_of(al * ga - be * be, s);
+    g = ga * r.S;
+    f = (r.OMC + be * r.S) / g;
+    e = (r.OMC - be * r.S) / g;
+}
+
+__device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double tau, double s, double &f,
+                          double &g, double &e)
+{
+    if (flow == HFS_FLOW_LEMMA2) {
+        const double om = sqrt(axis_omega2(p, dim, axis, tau));
+        double sh, ch;
+        sincos(0.5 * om * s, &sh, &ch);
+        g = 2.0 * sh * ch / om;
+        f = om * sh / ch;
+        e = f;
+    } else if (flow == HFS_FLOW_CF4) {
+        const double r3 = 0.28867513459481288225;  // sqrt(3)/6
+        const double al = 0.5 - 2.0 * r3;          // 1/2 - 1/sqrt(3)
+        const double be = 1.0 - al;
+        const double w1 = axis_omega2(p, dim, axis, tau + (0.5 - r3) * s);
+        const double w2 = axis_omega2(p, dim, axis, tau + (0.5 + r3) * s);
+        fge_thm2(al * w1 + be * w2, be * w1 + al * w2, s, f, g, e);
+    } else {
+        const double r15 = 0.38729833462074168852;  // sqrt(15)/10
+        const double w1 = axis_omega2(p, dim, axis, tau + (0.5 - r15) * s);
+        const double w2 = axis_omega2(p, dim, axis, tau + 0.5 * s);
+        const double w3 = axis_omega2(p, dim, axis, tau + (0.5 + r15) * s);
+        const double s2 = s * s;
+        const double avg = 5.0 * w1 + 8.0 * w2 + 5.0 * w3;
+        const double al = avg / 18.0 + s2 / 486.0 * (4.25 * (w1 * w1 + w3 * w3) + 8.0 * w2 * w2 + w1 * w2 +
+                                                     w2 * w3 - 18.5 * w1 * w3);
+        const double be = s * 1.29099444873580562839 * (w3 - w1) * (1.0 / 12.0 + s2 / 3240.0 * avg);  // sqrt(5/3)
+        const double ga = 1.0 + s2 / 54.0 * (w1 - 2.0 * w2 + w3);
+        fge_thm1(al, be, ga, s, f, g, e);
+    }
+    // mass: the mu-problem is the mu = 1 problem conjugated by diag(1, mu)
+    f *= p.mu;
+    e *= p.mu;
+    g /= p.mu;
+}
+
+// one thread per (instance, stage in chunk)
+__global__ void stage_flow_kernel(const DevInst *__restrict__ inst, int64_t count, int dim, SchedConst sc,
+                                  const double *__restrict__ t_dev, double t_off, int64_t nstage,
+                                  StageFGE *__restrict__ out, unsigned *status)
+{
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= count * nstage) return;
+    const int64_t i = gid / nstage;
+    const int64_t sg = gid - i * nstage;
+    const int64_t n = sg / sc.m;
+    const int st = (int)(sg - n * sc.m);
+    const double t0 = *t_dev + t_off;
+    const double tau = t0 + (double)n * sc.h + sc.h * sc.cuma[st];
+    const double s = sc.a[st] * sc.h;
+    const DevInst p = inst[i];
+    for (int d = 0; d < dim; ++d) {
+        double f, g, e;
+        stage_fge(p, dim, d, sc.flow, tau, s, f, g, e);
+        if (!isfinite(f) || !isfinite(g) || !isfinite(e)) atomicOr(status, (unsigned)ST_NONFINITE);
+        StageFGE r;
+        r.f = f;
+        r.g = g;
+        r.e = e;
+        r.tau = tau;
+        out[(i * nstage + sg) * dim + d] = r;
+    }
+}
+
+// kick coefficient kappa, B sum and drift g of sub-stage j on axis d
+__device__ void merged_coeffs(const DevInst &p, int dim, int d, const SchedConst &sc, double t0, int64_t j,
+                              int64_t nstage, const StageFGE *__restrict__ fge_i, double &kappa, double &bs,
+                              double &g)
+{
+    const int64_t mm = sc.m;
+    const int64_t r = j % mm;
+    if (r == 0) bs = (j > 0 ? sc.b[mm] : 0.0) + (j < nstage ? sc.b[0] : 0.0);
+    else bs = sc.b[r];
+    if (sc.split == HFS_SPLIT_HO) {
+        kappa = 0.0;
+        if (j >= 1) kappa += fge_i[(j - 1) * dim + d].f;
+        if (j < nstage) kappa += fge_i[j * dim + d].e;
+        g = (j < nstage) ? fge_i[j * dim + d].g : 0.0;
+    } else {
+        // F split: B carries mu omega^2(tau_j) x^2/2 with the time frozen at the stage boundary
+        const double tau = t0 + (double)(j / mm) * sc.h + sc.h * sc.cuma[r];
+        kappa = bs * sc.h * p.mu * axis_omega2(p, dim, d, tau);
+        g = (j < nstage) ? sc.a[r] * sc.h / p.mu : 0.0;
+    }
+}
+
+__device__ __forceinline__ void split_hi_lo(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__device__ __forceinline__ double frac1(double v) { return v - rint(v); }
+
+constexpr double kPi = 3.14159265358979323846;
+
+// one thread per (instance, sub-stage j in [0, nstage]) -- 1D records
+template <typename RecT>
+__global__ void records1d_kernel(const DevInst *__restrict__ inst, int64_t count, SchedConst sc,
+                                 const double *__restrict__ t_dev, double t_off, int64_t nstage,
+                                 const StageFGE *__restrict__ fge, RecT *__restrict__ rec, unsigned *status)
+{
+    const int64_t nrec = nstage + 1;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= count * nrec) return;
+    const int64_t i = gid / nrec;
+    const int64_t j = gid - i * nrec;
+    const DevInst p = inst[i];
+    const double t0 = *t_dev + t_off;
+    double kappa, bs, g;
+    merged_coeffs(p, 1, 0, sc, t0, j, nstage, fge + i * nstage, kappa, bs, g);
+    const double K2 = kappa * p.dx[0] * p.dx[0] / (4.0 * kPi);
+    const double K1 = kappa * p.xc[0] * p.dx[0] / (2.0 * kPi);
+    const double K0 = frac1(kappa * p.xc[0] * p.xc[0] / (4.0 * kPi));
+    const double G = g * kPi / (p.len[0] * p.len[0]);
+    const double SB = bs * sc.h / (2.0 * kPi);
+    if (!isfinite(K2) || !isfinite(G) || !isfinite(K1)) atomicOr(status, (unsigned)ST_NONFINITE);
+    RecT r;
+    if constexpr (sizeof(RecT) == sizeof(RecF)) {
+        split_hi_lo(K2, r.k2hi, r.k2lo);
+        split_hi_lo(K1, r.k1hi, r.k1lo);
+        r.k0 = (float)K0;
+        r.sb2pi = (float)SB;
+        split_hi_lo(G, r.ghi, r.glo);
+    } else {
+        r.k2 = K2;
+        r.k1 = K1;
+        r.k0 = K0;
+        r.sb2pi = SB;
+        r.g = G;
+        r.pad = 0.0;
+    }
+    rec[gid] = r;
+}
+
+// 3D records (symmetric boxes): one per sub-stage, all three axes
+template <typename RecT>
+__global__ void records3d_kernel(const DevInst *__restrict__ inst, SchedConst sc, const double *__restrict__ t_dev,
+                                 double t_off, int64_t nstage, const StageFGE *__restrict__ fge,
+                                 RecT *__restrict__ rec, unsigned *status)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j > nstage) return;
+    const DevInst p = inst[0];
+    const double t0 = *t_dev + t_off;
+    RecT r;
+    double SB = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double kappa, bs, g;
+        merged_coeffs(p, 3, d, sc, t0, j, nstage, fge, kappa, bs, g);
+        const double K2 = kappa * p.dx[d] * p.dx[d] / (4.0 * kPi);
+        const double G = g * kPi / (p.len[d] * p.len[d]);
+        SB = bs * sc.h / (2.0 * kPi);
+        if (!isfinite(K2) || !isfinite(G)) atomicOr(status, (unsigned)ST_NONFINITE);
+        if constexpr (sizeof(r.k2[0]) == sizeof(float)) {
+            split_hi_lo(K2, r.k2[d], r.k2lo[d]);
+            split_hi_lo(G, r.g[d], r.glo[d]);
+        } else {
+            r.k2[d] = K2;
+            r.g[d] = G;
+            r.k2lo[d] = 0.0;
+            r.glo[d] = 0.0;
+        }
+    }
+    r.sb2pi = SB;
+    rec[j] = r;
+}
+
+__global__ void set_time_kernel(double *t_dev, double t) { *t_dev = t; }
+__global__ void advance_time_kernel(double *t_dev, double dt) { *t_dev += dt; }
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const SchedConst &sc, const double *t_dev,
+                              double t_off, int64_t nstage, StageFGE *out, unsigned *status, cudaStream_t st)
+{
+    const int64_t n = count * nstage;
+    if (n == 0) return cudaSuccess;
+    stage_flow_kernel<<<blocks_for(n, 128), 128, 0, st>>>(inst, count, dim, sc, t_dev, t_off, nstage, out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records1d(bool fp64, const DevInst *inst, int64_t count, const SchedConst &sc, const double *t_dev,
+                             double t_off, int64_t nstage, const StageFGE *fge, void *rec, unsigned *status,
+                             cudaStream_t st)
+{
+    const int64_t n = count * (nstage + 1);
+    if (fp64)
+        records1d_kernel<RecD><<<blocks_for(n, 128), 128, 0, st>>>(inst, count, sc, t_dev, t_off, nstage, fge,
+                                                                    (RecD *)rec, status);
+    else
+        records1d_kernel<RecF><<<blocks_for(n, 128), 128, 0, st>>>(inst, count, sc, t_dev, t_off, nstage, fge,
+                                                                    (RecF *)rec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records3d(bool fp64, const DevInst *inst, const SchedConst &sc, const double *t_dev, double t_off,
+                             int64_t nstage, const StageFGE *fge, void *rec, unsigned *status, cudaStream_t st)
+{
+    const int64_t n = nstage + 1;
+    if (fp64)
+        records3d_kernel<Rec3D><<<blocks_for(n, 128), 128, 0, st>>>(inst, sc, t_dev, t_off, nstage, fge,
+                                                                     (Rec3D *)rec, status);
+    else
+        records3d_kernel<Rec3F><<<blocks_for(n, 128), 128, 0, st>>>(inst, sc, t_dev, t_off, nstage, fge,
+                                                                     (Rec3F *)rec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(double *t_dev, double t, cudaStream_t st)
+{
+    set_time_kernel<<<1, 1, 0, st>>>(t_dev, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_time(double *t_dev, double dt, cudaStream_t st)
+{
+    advance_time_kernel<<<1, 1, 0, st>>>(t_dev, dt);
+    return cudaGetLastError();
+}
+
+}  // namespace hfs

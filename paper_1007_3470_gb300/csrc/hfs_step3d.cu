@@ -1,0 +1,337 @@
+// hfs_step3d.cu -- 3D Hermite-Fourier split step on an n^3 periodic grid
+// (n = 32, 64, 128; symmetric box), complex64 or complex128.
+//
+// The harmonic part sum_d (p_d^2 + omega_d^2(t) x_d^2)/2 separates by axis,
+// so each A stage is kick(f_d) . drift(g_d) . kick(e_d) per axis (Theorem 2
+// with omega_d = c_d omega(t)); the kicks of the three axes and the B flow
+// merge into one pointwise x-phase, the drifts into one k-space phase of the
+// 3D transform.  One sub-stage is four passes over the state, each a batch
+// of length-n line transforms held in registers (layout of hfs_fft.cuh):
+//   z-pass  forward FFT_z, k-phase sum_d G_d m_d^2 (and 1/n^3), inverse FFT_z
+//   y-pass  inverse FFT_y
+//   x-pass  inverse FFT_x, x-phase X_{j+1}, forward FFT_x
+//   y-pass  forward FFT_y
+// The x-pass owns contiguous lines (private padded shared memory); the y-
+// and z-passes own tiles of TX adjacent columns whose lanes interleave in
+// shared memory, so global accesses stay coalesced along x.
+#include <algorithm>
+
+#include "hfs_fft.cuh"
+#include "hfs_law.cuh"
+#include "hfs_phase.cuh"
+#include "hfs_sched.h"
+#include "hfs_step3d.h"
+
+namespace hfs {
+
+template <typename R> struct Rec3Of;
+template <> struct Rec3Of<float> { using type = Rec3F; };
+template <> struct Rec3Of<double> { using type = Rec3D; };
+
+template <int N> struct Geo3 {
+    static constexpr int E = 16;
+    static constexpr int T = N / E;                 // threads per line
+    static constexpr int G = kCtaThreads / T;       // x-lines per CTA
+    static constexpr int TX = (kCtaThreads / T < N) ? kCtaThreads / T : N;  // columns per y/z tile
+    static constexpr int TT = T * TX;               // threads of a y/z tile CTA
+};
+
+__device__ __forceinline__ float turns_q(int m, float hi, float lo) { return frac_turns((float)(m * m), hi, lo); }
+__device__ __forceinline__ double turns_q(int m, double c, double) { return frac_turns((double)m * m, c, 0.0); }
+
+enum : int { X_INV = 1, X_PHASE = 2, X_FWD = 4 };
+
+// ---------------------------------------------------------------------------
+// x-pass
+// ---------------------------------------------------------------------------
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(kCtaThreads) xpass3d(const Step3DArgs a, int64_t j)
+{
+    using Rec = typename Rec3Of<R>::type;
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int line = blockIdx.x * GEO::G + g;  // y + N z
+    const int y = line % N, z = line / N;
+    cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + g * smem_elems(N);
+    cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)line * N;
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    cpx<R> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = psi[t + T * e];
+    if constexpr (MODE & X_INV) FftPlan<N, E>::template run<true, R>(v, sm, t, tw);
+    if constexpr (MODE & X_PHASE) {
+        const Rec rc = reinterpret_cast<const Rec *>(a.rec)[j];
+        const DevInst &ip = *a.inst;
+        const int my = y - N / 2, mz = z - N / 2;
+        const R tyz = turns_q(my, rc.k2[1], rc.k2lo[1]) + turns_q(mz, rc.k2[2], rc.k2lo[2]);
+        const R dx = (R)ip.dx[0], vk = (R)ip.vi_k, eps = (R)ip.eps, sig = (R)ip.sigma;
+        const int vkind = (ip.eps != 0.0) ? ip.vi_kind : HFS_VI_NONE;
+        const R vyz = vi_eval(vkind, (R)my * (R)ip.dx[1], vk) + vi_eval(vkind, (R)mz * (R)ip.dx[2], vk);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int mx = t + T * e - N / 2;
+            R turns = turns_q(mx, rc.k2[0], rc.k2lo[0]) + tyz;
+            const R dens = v[e].x * v[e].x + v[e].y * v[e].y;
+            const R F = sig * dens + eps * (vi_eval(vkind, (R)mx * dx, vk) + vyz);
+            turns += (R)rc.sb2pi * F;
+            v[e] = apply_turns(v[e], turns, R(1));
+        }
+    }
+    if constexpr (MODE & X_FWD) FftPlan<N, E>::template run<false, R>(v, sm, t, tw);
+    bool bad = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        psi[t + T * e] = v[e];
+        bad |= !(isfinite(v[e].x) && isfinite(v[e].y));
+    }
+    if ((MODE & X_PHASE) && !(MODE & X_FWD) && bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// y-pass: one CTA = fixed z, TX adjacent x columns; lines along y
+// ---------------------------------------------------------------------------
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(kCtaThreads) ypass3d(const Step3DArgs a)
+{
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T, TX = GEO::TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int l = threadIdx.x % TX, t = threadIdx.x / TX;
+    const int z = blockIdx.y, x0 = blockIdx.x * TX;
+    cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
+    cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)z * N * N + x0 + l;
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    cpx<R> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N];
+    FftPlan<N, E>::template run<INV, R, TX>(v, sm, t, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N] = v[e];
+}
+
+// ---------------------------------------------------------------------------
+// z-pass: one CTA = fixed y, TX adjacent x columns; forward FFT_z, k-phase,
+// inverse FFT_z
+// ---------------------------------------------------------------------------
+template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpass3d(const Step3DArgs a, int64_t j)
+{
+    using Rec = typename Rec3Of<R>::type;
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T, TX = GEO::TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int l = threadIdx.x % TX, t = threadIdx.x / TX;
+    const int y = blockIdx.y, x = blockIdx.x * TX + l;
+    cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
+    cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)y * N + x;
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    cpx<R> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
+    FftPlan<N, E>::template run<false, R, TX>(v, sm, t, tw);
+    {
+        const Rec rc = reinterpret_cast<const Rec *>(a.rec)[j];
+        const int mx = (x < N / 2) ? x : x - N;
+        const int my = (y < N / 2) ? y : y - N;
+        const R txy = turns_q(mx, rc.g[0], rc.glo[0]) + turns_q(my, rc.g[1], rc.glo[1]);
+        const R scale = R(1) / (R(N) * R(N) * R(N));
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int kz = t + T * e;
+            const int mz = (kz < N / 2) ? kz : kz - N;
+            v[e] = apply_turns(v[e], txy + turns_q(mz, rc.g[2], rc.glo[2]), scale);
+        }
+    }
+    FftPlan<N, E>::template run<true, R, TX>(v, sm, t, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N * N] = v[e];
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: norm, potential + interaction, and the kinetic energy as a sum
+// over axes of 1D Parseval sums  sum_x |d_d u|^2 = (1/n) sum_k k_d^2 |F_d u|^2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_add2(double a0, double a1, double *out, double *red)
+{
+    __syncthreads();
+    red[2 * threadIdx.x] = a0;
+    red[2 * threadIdx.x + 1] = a1;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            red[2 * threadIdx.x] += red[2 * (threadIdx.x + s)];
+            red[2 * threadIdx.x + 1] += red[2 * (threadIdx.x + s) + 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out, red[0]);
+        atomicAdd(out + 1, red[1]);
+    }
+}
+
+template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) diagx3d(const Diag3DArgs a)
+{
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int line = blockIdx.x * GEO::G + g;
+    const int y = line % N, z = line / N;
+    cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + g * smem_elems(N);
+    const cpx<R> *psi = reinterpret_cast<const cpx<R> *>(a.psi) + (int64_t)line * N;
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const DevInst &ip = *a.inst;
+    const double w2 = law_omega2(ip, *a.t_dev);
+    const double dx = ip.dx[0];
+    const double xy = (y - N / 2) * ip.dx[1], xz = (z - N / 2) * ip.dx[2];
+    const double vyz = 0.5 * ip.mu * w2 * (ip.axis_scale[1] * ip.axis_scale[1] * xy * xy +
+                                           ip.axis_scale[2] * ip.axis_scale[2] * xz * xz) +
+                       ip.eps * (vi_eval(ip.vi_kind, xy, ip.vi_k) + vi_eval(ip.vi_kind, xz, ip.vi_k));
+    cpx<R> v[E];
+    double nrm = 0.0, en = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        v[e] = psi[t + T * e];
+        const double xx = (t + T * e - N / 2) * dx;
+        const double d = (double)v[e].x * v[e].x + (double)v[e].y * v[e].y;
+        const double V = 0.5 * ip.mu * w2 * ip.axis_scale[0] * ip.axis_scale[0] * xx * xx +
+                         ip.eps * vi_eval(ip.vi_kind, xx, ip.vi_k) + vyz;
+        nrm += d;
+        en += V * d + 0.5 * ip.sigma * d * d;
+    }
+    FftPlan<N, E>::template run<false, R>(v, sm, t, tw);
+    const double ku = 2.0 * 3.14159265358979323846 / ip.len[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        const double kk = ku * ((k < N / 2) ? k : k - N);
+        kin += kk * kk * ((double)v[e].x * v[e].x + (double)v[e].y * v[e].y);
+    }
+    const double dv = ip.dx[0] * ip.dx[1] * ip.dx[2];
+    block_add2(nrm * dv, (en + kin / N / (2.0 * ip.mu)) * dv, a.out, reinterpret_cast<double *>(smem_raw));
+}
+
+// kinetic energy along y (AXIS = 1) or z (AXIS = 2)
+template <typename R, int N, int AXIS> __global__ void __launch_bounds__(kCtaThreads) diagyz3d(const Diag3DArgs a)
+{
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T, TX = GEO::TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int l = threadIdx.x % TX, t = threadIdx.x / TX;
+    const int other = blockIdx.y, x = blockIdx.x * TX + l;
+    const int64_t stride = (AXIS == 1) ? N : (int64_t)N * N;
+    const int64_t base = (AXIS == 1) ? (int64_t)other * N * N + x : (int64_t)other * N + x;
+    cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
+    const cpx<R> *psi = reinterpret_cast<const cpx<R> *>(a.psi) + base;
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const DevInst &ip = *a.inst;
+    cpx<R> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * stride];
+    FftPlan<N, E>::template run<false, R, TX>(v, sm, t, tw);
+    const double ku = 2.0 * 3.14159265358979323846 / ip.len[AXIS];
+    double kin = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        const double kk = ku * ((k < N / 2) ? k : k - N);
+        kin += kk * kk * ((double)v[e].x * v[e].x + (double)v[e].y * v[e].y);
+    }
+    const double dv = ip.dx[0] * ip.dx[1] * ip.dx[2];
+    block_add2(0.0, kin / N / (2.0 * ip.mu) * dv, a.out, reinterpret_cast<double *>(smem_raw));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+bool step3d_supported(int nx, int ny, int nz) { return nx == ny && ny == nz && (nx == 32 || nx == 64 || nx == 128); }
+
+template <typename R, int N> static size_t xsmem() { return (size_t)Geo3<N>::G * smem_elems(N) * sizeof(cpx<R>); }
+template <typename R, int N> static size_t tsmem()
+{
+    const size_t a = (size_t)Geo3<N>::TX * N * sizeof(cpx<R>);
+    const size_t b = 2 * sizeof(double) * Geo3<N>::TT;
+    return a > b ? a : b;
+}
+
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int N> static cudaError_t run3d(const Step3DArgs &a, cudaStream_t st)
+{
+    using GEO = Geo3<N>;
+    const size_t xs = xsmem<R, N>(), ts = tsmem<R, N>();
+    static bool prepared = false;
+    if (!prepared) {
+        cudaError_t e;
+        if ((e = allow_smem(xpass3d<R, N, X_PHASE | X_FWD>, xs)) != cudaSuccess) return e;
+        if ((e = allow_smem(xpass3d<R, N, X_INV | X_PHASE | X_FWD>, xs)) != cudaSuccess) return e;
+        if ((e = allow_smem(xpass3d<R, N, X_INV | X_PHASE>, xs)) != cudaSuccess) return e;
+        if ((e = allow_smem(ypass3d<R, N, false>, ts)) != cudaSuccess) return e;
+        if ((e = allow_smem(ypass3d<R, N, true>, ts)) != cudaSuccess) return e;
+        if ((e = allow_smem(zpass3d<R, N>, ts)) != cudaSuccess) return e;
+        prepared = true;
+    }
+    const dim3 xg(N * N / GEO::G), tg(N / GEO::TX, N);
+    xpass3d<R, N, X_PHASE | X_FWD><<<xg, kCtaThreads, xs, st>>>(a, 0);
+    ypass3d<R, N, false><<<tg, GEO::TT, ts, st>>>(a);
+    for (int64_t j = 0; j < a.nstage; ++j) {
+        zpass3d<R, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        ypass3d<R, N, true><<<tg, GEO::TT, ts, st>>>(a);
+        if (j + 1 < a.nstage) {
+            xpass3d<R, N, X_INV | X_PHASE | X_FWD><<<xg, kCtaThreads, xs, st>>>(a, j + 1);
+            ypass3d<R, N, false><<<tg, GEO::TT, ts, st>>>(a);
+        } else {
+            xpass3d<R, N, X_INV | X_PHASE><<<xg, kCtaThreads, xs, st>>>(a, j + 1);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename R, int N> static cudaError_t diag3d(const Diag3DArgs &a, cudaStream_t st)
+{
+    using GEO = Geo3<N>;
+    const size_t xs = xsmem<R, N>(), ts = tsmem<R, N>();
+    static bool prepared = false;
+    if (!prepared) {
+        cudaError_t e;
+        if ((e = allow_smem(diagx3d<R, N>, std::max(xs, 2 * sizeof(double) * kCtaThreads))) != cudaSuccess) return e;
+        if ((e = allow_smem(diagyz3d<R, N, 1>, ts)) != cudaSuccess) return e;
+        if ((e = allow_smem(diagyz3d<R, N, 2>, ts)) != cudaSuccess) return e;
+        prepared = true;
+    }
+    cudaError_t e = cudaMemsetAsync(a.out, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const dim3 xg(N * N / GEO::G), tg(N / GEO::TX, N);
+    diagx3d<R, N><<<xg, kCtaThreads, std::max(xs, 2 * sizeof(double) * kCtaThreads), st>>>(a);
+    diagyz3d<R, N, 1><<<tg, GEO::TT, ts, st>>>(a);
+    diagyz3d<R, N, 2><<<tg, GEO::TT, ts, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step3d(bool fp64, const Step3DArgs &a, cudaStream_t st)
+{
+    switch (a.n) {
+    case 32: return fp64 ? run3d<double, 32>(a, st) : run3d<float, 32>(a, st);
+    case 64: return fp64 ? run3d<double, 64>(a, st) : run3d<float, 64>(a, st);
+    case 128: return fp64 ? run3d<double, 128>(a, st) : run3d<float, 128>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_diag3d(bool fp64, const Diag3DArgs &a, cudaStream_t st)
+{
+    switch (a.n) {
+    case 32: return fp64 ? diag3d<double, 32>(a, st) : diag3d<float, 32>(a, st);
+    case 64: return fp64 ? diag3d<double, 64>(a, st) : diag3d<float, 64>(a, st);
+    case 128: return fp64 ? diag3d<double, 128>(a, st) : diag3d<float, 128>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace hfs

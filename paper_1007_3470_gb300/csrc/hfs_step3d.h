@@ -1,0 +1,32 @@
+// hfs_step3d.h -- the 3D split step (diagonal trap x^T M(t) x, separable
+// per axis) and its diagnostics (library-internal).
+#pragma once
+
+#include "hfs_internal.cuh"
+
+namespace hfs {
+
+struct Step3DArgs {
+    void *psi;  // cpx<R>[n^3], x fastest
+    const DevInst *inst;
+    const void *rec;  // Rec3F / Rec3D [nstage + 1]
+    int64_t nstage;
+    const void *tw;
+    unsigned *status;
+    int n;  // points per axis
+};
+
+struct Diag3DArgs {
+    const void *psi;
+    const DevInst *inst;
+    const void *tw;
+    const double *t_dev;
+    double *out;  // [2]: norm, energy
+    int n;
+};
+
+bool step3d_supported(int nx, int ny, int nz);
+cudaError_t launch_step3d(bool fp64, const Step3DArgs &a, cudaStream_t st);
+cudaError_t launch_diag3d(bool fp64, const Diag3DArgs &a, cudaStream_t st);
+
+}  // namespace hfs

@@ -1,0 +1,62 @@
+"""GPU parity of the 3D split step (diagonal trap (1, 1.5^2, 2^2)(1 + 0.3 sin t)^2,
+sigma=100, eps sum_d cos 2x_d) against the FP64 oracle, and FP32 vs FP64 on
+the device at 128^3."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1007_3470_gb300 import workloads as W
+from tests.gpu_helpers import TOL_C128, TOL_C64, budget, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu3d(inst, psi0, steps, precision, chunk=512):
+    from paper_1007_3470_gb300 import hfs
+    s = hfs.Solver([inst], dim=3, precision=precision, chunk_steps=chunk)
+    s.set_schedule(inst.h, inst.scheme, inst.ho_flow)
+    s.set_psi(psi0.ravel())
+    s.step(steps)
+    out = s.split(s.get_psi())[0]
+    assert s.status() == hfs.HFS_OK
+    nrm, en = s.norm()[0], s.energy()[0]
+    s.close()
+    return np.asarray(out), nrm, en
+
+
+@pytest.mark.parametrize("n", [32, 64])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_3d_vs_oracle(n, precision, tol):
+    need_gpu()
+    inst, psi0, _ = W.gpe_3d(n=n, h=0.005)
+    steps = 20
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    out, nrm, en = _gpu3d(inst, psi0, steps, precision)
+    assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+    p = O.Problem(**inst.as_dict())
+    rtol = 1e-12 if precision == "c128" else 3e-6
+    assert abs(nrm - O.norm(p, ref)) <= rtol
+    assert abs(en - O.energy(p, ref, steps * inst.h)) <= rtol * 10 * abs(en)
+
+
+def test_3d_128_fp32_vs_fp64_and_oracle():
+    need_gpu()
+    inst, psi0, _ = W.gpe_3d(n=128, h=0.005)
+    steps = 6
+    o32, n32, e32 = _gpu3d(inst, psi0, steps, "c64")
+    o64, n64, e64 = _gpu3d(inst, psi0, steps, "c128")
+    T = steps * inst.h
+    assert O.rel_l2(o32, o64) <= TOL_C64 * max(T, 1.0) * 0.1
+    assert abs(n32 - 1.0) < 3e-6 and abs(n64 - 1.0) < 1e-12
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    assert O.rel_l2(o64, ref) <= TOL_C128 * max(T, 1.0)
+
+
+def test_3d_chunked_equals_oracle():
+    """Several schedule chunks (chunk boundaries re-split the merged phases)."""
+    need_gpu()
+    inst, psi0, _ = W.gpe_3d(n=32, h=0.01)
+    steps = 13
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    out, _, _ = _gpu3d(inst, psi0, steps, "c128", chunk=4)
+    assert O.rel_l2(out, ref) <= budget(TOL_C128, steps * inst.h)

@@ -1,0 +1,241 @@
+"""GPU parity of the 1D split step (through the C ABI) against the FP64
+oracle on the same seeded inputs.  Bar: relative L2 error <= 1e-5 per unit
+time for the FP32 path, <= 1e-11 per unit time for the FP64 path."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1007_3470_gb300 import workloads as W
+from tests.gpu_helpers import TOL_C128, TOL_C64, budget, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(insts, psis, steps, precision, dt, comp="strang", flow=None, split=0, mode=None, chunk=512,
+             graphs=False, t0=0.0):
+    from paper_1007_3470_gb300 import hfs
+    s = hfs.Solver(insts, precision=precision, chunk_steps=chunk)
+    s.set_schedule(dt, comp, insts[0].ho_flow if flow is None else flow, split)
+    if mode is not None:
+        s.set_mode(*mode)
+    if graphs:
+        s.set_graphs(True)
+    if t0:
+        s.set_time(t0)
+    s.set_psi(psis)
+    s.step(steps)
+    out = [np.array(v) for v in s.split(s.get_psi())]
+    assert s.status() == hfs.HFS_OK
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_coherent_quartic_1d(precision, tol):
+    """N=256, [-16,16), omega=1, eps x^4, coherent state x0=1, Strang + exact
+    harmonic flow (Lemma 2), dt=0.01, 1000 steps (T=10)."""
+    need_gpu()
+    inst, psi0, steps = W.coherent_1d()
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    (out,) = _run_gpu([inst], [psi0], steps, precision, inst.h)
+    T = steps * inst.h
+    assert O.rel_l2(out, ref) <= budget(tol, T)
+
+
+@pytest.mark.parametrize("h", [0.04, 0.01])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_gpe_timedependent_magnus4_ni5(precision, tol, h):
+    """N=1024, [-20,20), omega(t)=1+0.5 sin 2t, sigma=10, eps cos 2x, CF4 +
+    Theorem 2 inside NI_5(8,4); T=10."""
+    need_gpu()
+    inst, psi0, steps = W.gpe_tdep_1d(h=h)
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    (out,) = _run_gpu([inst], [psi0], steps, precision, h, comp="ni5_84")
+    assert O.rel_l2(out, ref) <= budget(tol, steps * h)
+
+
+@pytest.mark.parametrize("comp,flow,split", [("srkn6_4", 1, 0), ("ni4_82", 1, 0), ("strang", 2, 0),
+                                             ("ni5_84", 2, 0), ("strang", 1, 1), ("srkn6_4", 1, 1)])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_schedule_variants(precision, tol, comp, flow, split):
+    need_gpu()
+    inst, psi0, _ = W.gpe_tdep_1d(h=0.02, n=512, scheme=comp, ho_flow=flow)
+    inst.a, inst.b = [-16.0], [16.0]
+    inst.split = split
+    psi0 = W.gaussian_1d(inst, x0=0.4)
+    steps = 100
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    (out,) = _run_gpu([inst], [psi0], steps, precision, inst.h, comp=comp, flow=flow, split=split)
+    assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_asymmetric_box_and_mass(precision, tol):
+    """A box not centred at 0 (K1, K0 terms of the chirp) and mu != 1."""
+    need_gpu()
+    inst = W.Instance(n=[512], a=[-9.0], b=[15.0], mu=1.7, omega_law=W.OMEGA_SIN, w0=1.2, law=[0.2, 1.3, 0.4],
+                      eps=0.05, vi_kind=W.VI_X4, sigma=3.0, ho_flow=W.FLOW_CF4, h=0.01)
+    psi0 = W.gaussian_1d(inst, x0=2.0, width2=0.7, p0=0.5)
+    steps = 200
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    (out,) = _run_gpu([inst], [psi0], steps, precision, inst.h)
+    assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_batched_mixed_sizes(precision, tol):
+    """A seeded sample of the batched workload (every size 128..4096, ragged
+    concatenation) vs the oracle instance by instance."""
+    need_gpu()
+    insts, psis, _ = W.batch_1d(count=48, seed=11)
+    steps = 60
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    outs = _run_gpu(insts, psis, steps, precision, 0.005)
+    T = steps * 0.005
+    errs = [O.rel_l2(o, r) for o, r in zip(outs, refs)]
+    assert max(errs) <= budget(tol, T), max(errs)
+    assert sorted({i.n[0] for i in insts}) == [128, 256, 512, 1024, 2048, 4096]
+
+
+def test_modes_graphs_and_plans_agree():
+    """Streaming (one step per launch), resident, graph replay and both plan
+    variants give the same FP32 result (bitwise for the launch modes)."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=40, seed=5)
+    steps = 30
+    base = _run_gpu(insts, psis, steps, "c64", 0.005)
+    stream = _run_gpu(insts, psis, steps, "c64", 0.005, mode=(hfs.HFS_MODE_STREAMING, 1))
+    stream4 = _run_gpu(insts, psis, steps, "c64", 0.005, mode=(hfs.HFS_MODE_STREAMING, 4))
+    graph = _run_gpu(insts, psis, steps, "c64", 0.005, graphs=True)
+    for a, b, c, d in zip(base, stream, stream4, graph):
+        assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+    s = hfs.Solver(insts, precision="c64", chunk_steps=64)
+    s.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    for n in (128, 256, 512, 1024, 2048):
+        s.set_plan(n, 8)
+    s.set_psi(psis)
+    s.step(steps)
+    alt = s.split(s.get_psi())
+    for a, b in zip(base, alt):
+        assert O.rel_l2(b, a) < 5e-6
+    s.close()
+
+
+def test_graph_replay_advances_time():
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=8, seed=9)
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, 40)
+    s = hfs.Solver(insts, precision="c64", chunk_steps=64)
+    s.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    s.set_graphs(True)
+    s.set_psi(psis)
+    for _ in range(4):
+        s.step(10)  # same graph replayed; the device-side time advances
+    assert abs(s.time - 0.2) < 1e-15
+    outs = s.split(s.get_psi())
+    assert max(O.rel_l2(o, r) for o, r in zip(outs, refs)) < TOL_C64
+
+
+def test_checkpoint_resume_bitwise():
+    """2n steps in one call equal n steps, a checkpoint (get/set psi + time)
+    and n more steps, bitwise, when the schedule chunks coincide."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=16, seed=3)
+    n = 25
+    a = hfs.Solver(insts, precision="c64", chunk_steps=n)
+    a.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    a.set_psi(psis)
+    a.step(2 * n)
+    full = a.get_psi()
+    b = hfs.Solver(insts, precision="c64", chunk_steps=n)
+    b.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    b.set_psi(psis)
+    b.step(n)
+    ck, t = b.get_psi(), b.time
+    c = hfs.Solver(insts, precision="c64", chunk_steps=n)
+    c.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    c.set_psi(ck)
+    c.set_time(t)
+    c.step(n)
+    assert np.array_equal(full, c.get_psi())
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-12), ("c64", 2e-5)])
+def test_time_reversibility(precision, tol):
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    inst, psi0, _ = W.gpe_tdep_1d(h=0.01, n=1024)
+    s = hfs.Solver([inst], precision=precision)
+    s.set_schedule(0.01, "ni5_84", hfs.HFS_FLOW_CF4)
+    s.set_psi([psi0])
+    s.step(100)
+    mid = s.get_psi()
+    s.set_schedule(-0.01, "ni5_84", hfs.HFS_FLOW_CF4)
+    s.step(100)
+    back = s.get_psi()
+    assert O.rel_l2(back, psi0) < tol
+    assert O.rel_l2(mid, psi0) > 1e-2
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_norm_and_energy_match_oracle(precision):
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=24, seed=21)
+    s = hfs.Solver(insts, precision=precision)
+    s.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    s.set_psi(psis)
+    s.step(40)
+    outs = [np.asarray(v, dtype=np.complex128) for v in s.split(s.get_psi())]
+    nrm, en = s.norm(), s.energy()
+    t = s.time
+    tol = 1e-12 if precision == "c128" else 2e-6
+    for i, inst in enumerate(insts):
+        p = O.Problem(**inst.as_dict())
+        assert abs(nrm[i] - O.norm(p, outs[i])) <= tol * abs(nrm[i])
+        assert abs(en[i] - O.energy(p, outs[i], t)) <= tol * 10 * max(1.0, abs(en[i]))
+        assert abs(nrm[i] - 1.0) < (1e-12 if precision == "c128" else 2e-6)  # norm conservation
+
+
+def test_eigenstate_phase_gpu():
+    """Hermite eigenstate h_4 of omega = 1.3 gains exp(-i 4.5 omega t)."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    omega = 1.3
+    inst = W.Instance(n=[256], a=[-12.0], b=[12.0], w0=omega, ho_flow=W.FLOW_LEMMA2, h=0.05)
+    x = inst.x()
+    xs = math.sqrt(omega) * x
+    H = [np.ones_like(xs), 2 * xs]
+    for k in range(1, 4):
+        H.append(2 * xs * H[k] - 2 * k * H[k - 1])
+    psi0 = omega ** 0.25 * H[4] * np.exp(-xs ** 2 / 2) / (math.pi ** 0.25 * math.sqrt(2.0 ** 4 * 24))
+    for precision, tol in (("c128", 1e-11), ("c64", 2e-5)):
+        s = hfs.Solver([inst], precision=precision)
+        s.set_schedule(0.05, "strang", hfs.HFS_FLOW_LEMMA2)
+        s.set_psi([psi0.astype(complex)])
+        s.step(400)
+        out = s.get_psi()
+        assert O.rel_l2(out, psi0 * np.exp(-1j * 4.5 * omega * 20.0)) < tol
+
+
+def test_errors_reported():
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    inst = W.Instance(n=[256], a=[-12.0], b=[12.0], w0=2.0, ho_flow=W.FLOW_LEMMA2, h=0.05)
+    s = hfs.Solver([inst], precision="c64")
+    s.set_schedule(2.0, "strang", hfs.HFS_FLOW_LEMMA2)  # |h| omega = 4 > pi
+    with pytest.raises(hfs.HfsError) as ei:
+        s.step(1)
+    assert ei.value.code == 3
+    s.set_schedule(0.05, "strang", hfs.HFS_FLOW_LEMMA2)
+    bad = np.zeros(256, complex)
+    bad[10] = np.nan
+    s.set_psi(bad)
+    s.step(2)
+    assert s.status() == 5  # HFS_ERR_NONFINITE
+    assert s.status() == 0  # cleared
