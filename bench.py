@@ -133,11 +133,13 @@ def run_native(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    insts, psis, _ = W.batch_1d(count=COUNT, seed=W.SEED + rank, h=DT, steps=STEPS)
-    gps, flops = algorithmic_counts(insts, STEPS)
-    solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS)
+    COUNT_, STEPS_ = args.count, args.time_steps
+    insts, psis, _ = W.batch_1d(count=COUNT_, seed=W.SEED + rank, h=DT, steps=STEPS_)
+    gps, flops = algorithmic_counts(insts, STEPS_)
+    solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS_)
     solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     tuned = solver.autotune(trial_steps=20) if args.autotune else None
+    hfs.hfs_set_profiling(solver.h, True)
     solver.set_graphs(True)
     host0 = np.concatenate([p.astype(np.complex64) for p in psis])
     pinned_in = torch.from_numpy(host0.view(np.float32)).pin_memory()
@@ -147,7 +149,7 @@ def run_native(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def one():
-        solver.step(STEPS)
+        solver.step(STEPS_)
 
     for _ in range(args.warmup):
         one()
@@ -157,6 +159,7 @@ def run_native(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    kern_ms = []
     with Clocks(local) as clk:
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -165,6 +168,8 @@ def run_native(args):
             evs[k][0].record(stream)
             one()
             evs[k][1].record(stream)
+            # fused step kernel alone (events recorded by the library on the same stream)
+            kern_ms.append(hfs.hfs_last_step_kernel_ms(solver.h))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if ws > 1:
@@ -172,15 +177,15 @@ def run_native(args):
     ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(ms)
     st = solver.status()
-    # the dominant kernel: one resident launch per solve (all 500 steps on chip)
-    step_ms = total_ms / args.steps
+    # the dominant kernel: one resident launch per solve (all time steps on chip)
+    step_ms = sum(kern_ms) / len(kern_ms)
     # end to end through the C ABI with host buffers
     e2e_ms = []
     for k in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hfs.hfs_set_psi(solver.h, pinned_in.data_ptr(), False)
-        solver.step(STEPS)
+        solver.step(STEPS_)
         hfs.hfs_get_psi(solver.h, pinned_out.data_ptr(), False)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step_ms = statistics.median(e2e_ms)
@@ -200,8 +205,8 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
-        "config": {"workload": "batch_1d_4096x500_c64", "instances": COUNT, "time_steps": STEPS, "dt": DT,
-                   "grid_sizes": "128..4096 uniform", "composition": "strang", "ho_flow": "magnus4_cf+thm2",
+        "config": {"workload": f"batch_1d_{COUNT_}x{STEPS_}_c64", "instances": COUNT_, "time_steps": STEPS_,
+                   "dt": DT, "grid_sizes": "128..4096 uniform", "composition": "strang", "ho_flow": "magnus4_cf+thm2",
                    "mode": "resident, graph-replayed", "l2": "flushed between steps (256 MiB write)",
                    "solves_per_s": ws * args.steps / (total_ms * 1e-3),
                    "plans_ept": tuned},
@@ -212,6 +217,7 @@ def run_native(args):
         "e2e": {"value": gps * ws / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
                 "h2d_bytes_per_step": int(host0.nbytes), "d2h_bytes_per_step": int(host0.nbytes)},
         "gpu_launches": 4 * args.steps,
+        "kernel_ms_per_launch": step_ms,
         "clocks": clk.summary(),
         "status": st,
         "wall_s": t_wall,
@@ -296,6 +302,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4, help="instances per grid size in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
+    ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -205,6 +205,17 @@ int hfs_set_plan(hfs_ctx_t ctx, int n, int elems_per_thread);
  * the size is absent). */
 int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_ept);
 
+/* ---- profiling -------------------------------------------------------- */
+
+/* enable != 0: record CUDA events on the context's stream around the fused
+ * step-kernel launches of every hfs_step() (also inside captured graphs). */
+int hfs_set_profiling(hfs_ctx_t ctx, int enable);
+
+/* Device time in ms from the first to the last fused step-kernel launch of
+ * the most recent hfs_step() (synchronises on its end event).  Errors:
+ * HFS_ERR_NOT_READY when profiling is off or no step ran. */
+int hfs_last_step_kernel_ms(hfs_ctx_t ctx, float *ms);
+
 const char *hfs_error_string(int status);
 
 #ifdef __cplusplus

@@ -58,6 +58,9 @@ struct hfs_ctx_s {
     std::map<int64_t, cudaGraphExec_t> graphs_by_n;
     uint64_t version = 0;  // bumps invalidate cached graphs
     std::vector<double> diag_host;
+    // profiling events around the fused step kernels
+    bool profiling = false, prof_valid = false;
+    cudaEvent_t kev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -188,6 +191,24 @@ int upload_tables(hfs_ctx_s *c)
     return HFS_OK;
 }
 
+// events recorded while the stream is being captured must become event-record
+// nodes of the graph (not fork/join markers), hence cudaEventRecordExternal
+cudaError_t record_prof(hfs_ctx_s *c, int which)
+{
+    return c->graphs ? cudaEventRecordWithFlags(c->kev[which], c->stream, cudaEventRecordExternal)
+                     : cudaEventRecord(c->kev[which], c->stream);
+}
+
+void drop_events(hfs_ctx_s *c)
+{
+    for (auto &e : c->kev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    c->prof_valid = false;
+}
+
 void drop_graphs(hfs_ctx_s *c)
 {
     for (auto &kv : c->graphs_by_n) cudaGraphExecDestroy(kv.second);
@@ -245,6 +266,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.status = status;
             const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64)));
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
+            if (c->profiling && done == 0) CK(record_prof(c, 0));
             for (int64_t s0 = 0; s0 < S; s0 += per) {
                 const int64_t s1 = std::min(S, s0 + per);
                 a.j0 = s0 * m;
@@ -253,6 +275,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
                 CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
                 CK(launch_step1d(fp64, a, grid, c->stream));
             }
+            if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
         } else {
             CK(launch_records3d(fp64, dinst, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
             Step3DArgs a{};
@@ -263,7 +286,9 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
             a.status = status;
             a.n = c->inst[0].n[0];
+            if (c->profiling && done == 0) CK(record_prof(c, 0));
             CK(launch_step3d(fp64, a, c->stream));
+            if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
         }
         done += S;
     }
@@ -384,7 +409,30 @@ void hfs_destroy(hfs_ctx_t c)
 {
     if (!c) return;
     drop_graphs(c);
+    drop_events(c);
     delete c;
+}
+
+int hfs_set_profiling(hfs_ctx_t c, int enable)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    drop_graphs(c);
+    drop_events(c);
+    c->profiling = enable != 0;
+    if (c->profiling) {
+        CK(cudaEventCreate(&c->kev[0]));
+        CK(cudaEventCreate(&c->kev[1]));
+    }
+    return HFS_OK;
+}
+
+int hfs_last_step_kernel_ms(hfs_ctx_t c, float *ms)
+{
+    if (!c || !ms) return HFS_ERR_INVALID_ARG;
+    if (!c->profiling || !c->prof_valid) return HFS_ERR_NOT_READY;
+    CK(cudaEventSynchronize(c->kev[1]));
+    CK(cudaEventElapsedTime(ms, c->kev[0], c->kev[1]));
+    return HFS_OK;
 }
 
 int hfs_set_stream(hfs_ctx_t c, void *stream)
@@ -579,6 +627,7 @@ int hfs_step(hfs_ctx_t c, int64_t nsteps)
         if (s) return s;
     }
     c->t += (double)nsteps * c->sc.h;
+    if (c->profiling) c->prof_valid = true;
     return HFS_OK;
 }
 

@@ -188,14 +188,25 @@ template <bool INV> __device__ __forceinline__ cpx<double> tw_mul(cpx<double> a,
 __device__ __forceinline__ int spad(int p) { return p + (p >> 4); }
 __host__ __device__ constexpr int smem_elems(int n) { return n + n / 16; }
 
-// Shared-memory slot of position p.  ILV == 1: the team owns a private,
-// padded region.  ILV > 1: ILV teams interleave element by element (the
-// caller offsets sm by its team index), so that a warp whose lanes are
+// Shared-memory slots.  ILV == 1: the team owns a private region padded by
+// one slot per 16 values.  ILV > 1: ILV teams interleave element by element
+// (the caller offsets sm by its team index), so that a warp whose lanes are
 // different teams at the same position touches consecutive addresses.
-template <int ILV> __device__ __forceinline__ int sslot(int p)
+//
+// Every access pattern of a pass is a runtime base A plus a compile-time
+// offset c with (A mod 16) + (c mod 16) < 16 (true for all power-of-two
+// plans: A = t for the reads, A = (b - j) RAD + j for the writes), so
+// pad(A + c) = pad(A) + c + c/16 splits into one base register and an
+// immediate offset.
+template <int ILV> __device__ __forceinline__ int sbase(int a)
 {
-    if constexpr (ILV == 1) return spad(p);
-    else return p * ILV;
+    if constexpr (ILV == 1) return a + (a >> 4);
+    else return a * ILV;
+}
+template <int ILV> __host__ __device__ constexpr int soff(int c)
+{
+    if constexpr (ILV == 1) return c + (c >> 4);
+    else return c * ILV;
 }
 
 // One Stockham pass; see the layout contract at the top of the file.
@@ -206,6 +217,14 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
     constexpr int T = N / E;
     constexpr int Q = E / RAD;
     static_assert(E % RAD == 0, "radix must divide the elements per thread");
+    // The twiddles of a thread are the same at every time step; without this
+    // opaque copy of the table pointer the compiler hoists all of them out of
+    // the time loop and keeps every pass's twiddles live in registers.
+    const typename TwOf<R>::type *twp = tw;
+    asm volatile("" : "+l"(twp));
+    // likewise the forward and inverse transforms compute identical integer
+    // offsets; recomputing them per pass is cheaper than holding them live
+    asm volatile("" : "+r"(t));
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         cpx<R> a[RAD];
@@ -215,23 +234,25 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
         const int j = b & (NS - 1);
         if constexpr (NS > 1) {
             constexpr int STRIDE = N / (NS * RAD);
+            const int js = j * STRIDE;
 #pragma unroll
-            for (int r = 1; r < RAD; ++r) a[r] = tw_mul<INV>(a[r], tw, j * r * STRIDE);
+            for (int r = 1; r < RAD; ++r) a[r] = tw_mul<INV>(a[r], twp, js * r);
         }
         dft_any<RAD, INV>(a);
         if constexpr (LAST) {
 #pragma unroll
             for (int r = 0; r < RAD; ++r) v[q + r * Q] = a[r];
         } else {
-            const int base = (b - j) * RAD + j;  // (b div NS) * NS * RAD + (b mod NS)
+            cpx<R> *w = sm + sbase<ILV>((b - j) * RAD + j);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) sm[sslot<ILV>(base + r * NS)] = a[r];
+            for (int r = 0; r < RAD; ++r) w[soff<ILV>(r * NS)] = a[r];
         }
     }
     if constexpr (!LAST) {
         __syncthreads();
+        const cpx<R> *rd = sm + sbase<ILV>(t);
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = sm[sslot<ILV>(t + T * e)];
+        for (int e = 0; e < E; ++e) v[e] = rd[soff<ILV>(T * e)];
         __syncthreads();
     }
 }

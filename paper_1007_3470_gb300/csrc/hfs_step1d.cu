@@ -46,6 +46,21 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
     return tp;
 }
 
+// Opaque dependence on a group of register values: work on later groups
+// cannot be scheduled before this point, so the phase loops below keep one
+// group of PHASE_GROUP elements in flight instead of interleaving all E.
+constexpr int PHASE_GROUP = 4;
+template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
+{
+#pragma unroll
+    for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+f"(v[e].x), "+f"(v[e].y));
+}
+template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E], int e0)
+{
+#pragma unroll
+    for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+d"(v[e].x), "+d"(v[e].y));
+}
+
 // merged x-phase X_j on the register layout (position t + T e)
 template <int N, int E>
 __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp)
@@ -53,6 +68,7 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
     constexpr int T = N / E;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
+        if (e % PHASE_GROUP == 0) fence_group(v, e);
         const int m = t + T * e - N / 2;
         const float mf = (float)m;
         float turns = frac_turns((float)(m * m), rc.k2hi, rc.k2lo);
@@ -89,6 +105,7 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E
     constexpr int T = N / E;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
+        if (e % PHASE_GROUP == 0) fence_group(v, e);
         const int k = t + T * e;
         const int m = (k < N / 2) ? k : k - N;
         const float turns = frac_turns((float)(m * m), rc.ghi, rc.glo);
@@ -130,10 +147,16 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 
     for (int64_t j = a.j0; j < a.j1; ++j) {
         const Rec rc = rec[j];
-        xphase<N, E>(v, t, rc, tp);
-        FftPlan<N, E>::template run<false, R>(v, sm, t, tw);
-        kphase<N, E>(v, t, rc);
-        FftPlan<N, E>::template run<true, R>(v, sm, t, tw);
+        // Position-dependent values (m^2, x, V_I(x)) are the same at every
+        // step; an opaque copy of t makes the compiler recompute them (a few
+        // integer and SFU operations) instead of holding 3E of them live
+        // across the whole time loop.
+        int tl = t;
+        asm volatile("" : "+r"(tl));
+        xphase<N, E>(v, tl, rc, tp);
+        FftPlan<N, E>::template run<false, R>(v, sm, tl, tw);
+        kphase<N, E>(v, tl, rc);
+        FftPlan<N, E>::template run<true, R>(v, sm, tl, tw);
     }
     if (a.final_x) {
         const Rec rc = rec[a.j1];
@@ -155,7 +178,10 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         X(256, 8) X(128, 8)
 
 // FP32: two CTAs per SM (128 registers); FP64 parity mode: one
-template <typename R> struct MinCtas { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
+#ifndef HFS_STEP1D_MIN_CTAS
+#define HFS_STEP1D_MIN_CTAS 2
+#endif
+template <typename R> struct MinCtas { static constexpr int value = sizeof(R) == 4 ? HFS_STEP1D_MIN_CTAS : 1; };
 
 template <typename R>
 __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(const Step1DArgs a)

@@ -34,7 +34,8 @@ COMPOSITIONS = {"strang": HFS_COMP_STRANG, "srkn6_4": HFS_COMP_SRKN6_4, "ni4_82"
 EXPORTS = ("hfs_create", "hfs_destroy", "hfs_set_stream", "hfs_state_size", "hfs_instance_offset",
            "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_graphs",
            "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi", "hfs_step", "hfs_norm",
-           "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_autotune", "hfs_error_string")
+           "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_autotune", "hfs_set_profiling",
+           "hfs_last_step_kernel_ms", "hfs_error_string")
 
 
 class hfs_instance(ctypes.Structure):
@@ -92,6 +93,8 @@ def lib():
             "hfs_sync_status": [vp],
             "hfs_set_plan": [vp, i32, i32],
             "hfs_autotune": [vp, i32, ctypes.POINTER(ctypes.c_int32)],
+            "hfs_set_profiling": [vp, i32],
+            "hfs_last_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
             "hfs_error_string": [i32],
         }
         for name, args in sig.items():
@@ -244,6 +247,16 @@ def hfs_autotune(h, trial_steps: int) -> list[int]:
     best = (ctypes.c_int32 * 6)()
     _check(lib().hfs_autotune(h, trial_steps, best), "hfs_autotune")
     return list(best)
+
+
+def hfs_set_profiling(h, enable: bool):
+    _check(lib().hfs_set_profiling(h, 1 if enable else 0), "hfs_set_profiling")
+
+
+def hfs_last_step_kernel_ms(h) -> float:
+    ms = ctypes.c_float()
+    _check(lib().hfs_last_step_kernel_ms(h, ctypes.byref(ms)), "hfs_last_step_kernel_ms")
+    return ms.value
 
 
 # --- convenience owner of the caller-side buffers ------------------------------

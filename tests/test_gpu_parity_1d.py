@@ -239,3 +239,23 @@ def test_errors_reported():
     s.step(2)
     assert s.status() == 5  # HFS_ERR_NONFINITE
     assert s.status() == 0  # cleared
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_profiling_events(graphs):
+    """The step-kernel timing hook works with and without graph replay."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=16, seed=4)
+    s = hfs.Solver(insts, precision="c64", chunk_steps=32)
+    s.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    with pytest.raises(hfs.HfsError):
+        hfs.hfs_last_step_kernel_ms(s.h)
+    hfs.hfs_set_profiling(s.h, True)
+    s.set_graphs(graphs)
+    s.set_psi(psis)
+    for _ in range(3):
+        s.step(20)
+        ms = hfs.hfs_last_step_kernel_ms(s.h)
+        assert 0.0 < ms < 1e4
+    assert s.status() == hfs.HFS_OK
