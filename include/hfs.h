@@ -216,6 +216,43 @@ int hfs_set_profiling(hfs_ctx_t ctx, int enable);
  * HFS_ERR_NOT_READY when profiling is off or no step ran. */
 int hfs_last_step_kernel_ms(hfs_ctx_t ctx, float *ms);
 
+/* ---- allocation-free batched step -------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- code that runs where cudaMalloc is
+ * not allowed or not wanted (allocator or memory-pool callbacks, a device
+ * memory budget fixed at start-up, a host library that is only handed a
+ * device pointer to the state) and therefore cannot provide the workspace
+ * that hfs_bind() needs.
+ *
+ * Advances `count` 1D instances (host array inst, n[0] in 128..4096) whose
+ * states are concatenated in the device buffer psi (complex64 for HFS_C64,
+ * complex128 for HFS_C128, 8/16-byte aligned; read and overwritten in place)
+ * by nsteps steps of size dt from time t0, with the given split, harmonic
+ * flow and built-in composition (HFS_COMP_CUSTOM is not accepted), on the
+ * given stream (NULL: legacy default stream).  Results equal those of
+ * hfs_step() with a 16-step schedule chunk.
+ *
+ * No device memory is allocated or freed: all scratch lives in one
+ * file-scope __device__ array of HFS_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until process exit.  The first call on a device
+ * resolves the array's address and fills its twiddle tables, synchronising
+ * the stream; make that first call before any stream capture.  Every call
+ * reuses the same array, which keeps the previous call's contents (the call
+ * clears what must start at zero): calls whose GPU work overlaps -- on
+ * different streams, or from different host threads -- race on it and must
+ * be serialised by the caller.
+ *
+ * wait != 0: synchronise the stream before returning and report a non-finite
+ * state as HFS_ERR_NONFINITE.  Errors: HFS_ERR_WORKSPACE when count exceeds
+ * HFS_NOALLOC_MAX_INSTANCES; HFS_ERR_INVALID_ARG, HFS_ERR_UNSUPPORTED,
+ * HFS_ERR_ALIGNMENT, HFS_ERR_STEP_TOO_LARGE, HFS_ERR_CUDA as for the
+ * context API. */
+#define HFS_NOALLOC_MAX_INSTANCES 512
+#define HFS_NOALLOC_SCRATCH_BYTES (6u << 20)
+int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *inst, int64_t count, int split, int ho_flow,
+                       int composition, double dt, double t0, int64_t nsteps, void *stream, int wait);
+
 const char *hfs_error_string(int status);
 
 #ifdef __cplusplus

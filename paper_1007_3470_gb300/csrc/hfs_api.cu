@@ -17,6 +17,66 @@
 
 using namespace hfs;
 
+namespace hfs {
+
+// BAB compositions into fixed arrays (m A-stages, m + 1 B-stages)
+int composition_fixed(int comp, double *a, double *b, int *m)
+{
+    // BAB compositions, b_1 applied first (Eq. LeapFrogB; Table 1)
+    switch (comp) {
+    case HFS_COMP_STRANG:
+        a[0] = 1.0; *m = 1;
+        b[0] = 0.5; b[1] = 0.5;
+        return 0;
+    case HFS_COMP_SRKN6_4: {
+        const double b1 = 0.0829844064174052, b2 = 0.396309801498368, b3 = -0.0390563049223486;
+        const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
+        const double a1 = 0.245298957184271, a2 = 0.604872665711080, a3 = 0.5 - (a1 + a2);
+        a[0] = a1; a[1] = a2; a[2] = a3; a[3] = a3; a[4] = a2; a[5] = a1; *m = 6;
+        b[0] = b1; b[1] = b2; b[2] = b3; b[3] = b4; b[4] = b3; b[5] = b2; b[6] = b1;
+        return 0;
+    }
+    case HFS_COMP_NI4_82: {
+        // Table 1 prints b_2 = 49/18; the (8,2) method's weights are the
+        // Lobatto weights 1/20, 49/180, 16/45, so b_2 = 49/180.
+        const double b1 = 1.0 / 20.0, b2 = 49.0 / 180.0, b3 = 1.0 - 2.0 * (b1 + b2);
+        const double a1 = 0.5 - sqrt(3.0 / 28.0), a2 = 0.5 - a1;
+        a[0] = a1; a[1] = a2; a[2] = a2; a[3] = a1; *m = 4;
+        b[0] = b1; b[1] = b2; b[2] = b3; b[3] = b2; b[4] = b1;
+        return 0;
+    }
+    case HFS_COMP_NI5_84: {
+        const double b1 = 0.811862738544516, b2 = -0.677480399532169, b3 = 0.5 - (b1 + b2);
+        const double a1 = -0.00758691311877447, a2 = 0.317218277973169, a3 = 1.0 - 2.0 * (a1 + a2);
+        a[0] = a1; a[1] = a2; a[2] = a3; a[3] = a2; a[4] = a1; *m = 5;
+        b[0] = b1; b[1] = b2; b[2] = b3; b[3] = b3; b[4] = b2; b[5] = b1;
+        return 0;
+    }
+    default:
+        return -1;
+    }
+}
+
+// upper bound of omega over [t0, t1] for the validity check
+double omega_bound(const hfs_instance &p, double t0, double t1)
+{
+    const double aw = fabs(p.w0);
+    switch (p.omega_law) {
+    case HFS_OMEGA_CONST:
+        return aw;
+    case HFS_OMEGA_SIN:
+        return aw * (1.0 + fabs(p.law[0]));
+    case HFS_OMEGA_COS_SQ:
+        return aw * sqrt(1.0 + fabs(p.law[0]));
+    case HFS_OMEGA_PULSE:
+        return aw * (1.0 + fabs(p.law[0]) * std::max(fabs(t0), fabs(t1)));
+    default:
+        return INFINITY;
+    }
+}
+
+}  // namespace hfs
+
 namespace {
 
 struct Layout {
@@ -75,57 +135,12 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 int composition_coeffs(int comp, std::vector<double> &a, std::vector<double> &b)
 {
-    // BAB compositions, b_1 applied first (Eq. LeapFrogB; Table 1)
-    switch (comp) {
-    case HFS_COMP_STRANG:
-        a = {1.0};
-        b = {0.5, 0.5};
-        return 0;
-    case HFS_COMP_SRKN6_4: {
-        const double b1 = 0.0829844064174052, b2 = 0.396309801498368, b3 = -0.0390563049223486;
-        const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
-        const double a1 = 0.245298957184271, a2 = 0.604872665711080, a3 = 0.5 - (a1 + a2);
-        a = {a1, a2, a3, a3, a2, a1};
-        b = {b1, b2, b3, b4, b3, b2, b1};
-        return 0;
-    }
-    case HFS_COMP_NI4_82: {
-        // Table 1 prints b_2 = 49/18; the (8,2) method's weights are the
-        // Lobatto weights 1/20, 49/180, 16/45, so b_2 = 49/180.
-        const double b1 = 1.0 / 20.0, b2 = 49.0 / 180.0, b3 = 1.0 - 2.0 * (b1 + b2);
-        const double a1 = 0.5 - sqrt(3.0 / 28.0), a2 = 0.5 - a1;
-        a = {a1, a2, a2, a1};
-        b = {b1, b2, b3, b2, b1};
-        return 0;
-    }
-    case HFS_COMP_NI5_84: {
-        const double b1 = 0.811862738544516, b2 = -0.677480399532169, b3 = 0.5 - (b1 + b2);
-        const double a1 = -0.00758691311877447, a2 = 0.317218277973169, a3 = 1.0 - 2.0 * (a1 + a2);
-        a = {a1, a2, a3, a2, a1};
-        b = {b1, b2, b3, b3, b2, b1};
-        return 0;
-    }
-    default:
-        return -1;
-    }
-}
-
-// upper bound of omega over [t0, t1] for the validity check
-double omega_bound(const hfs_instance &p, double t0, double t1)
-{
-    const double aw = fabs(p.w0);
-    switch (p.omega_law) {
-    case HFS_OMEGA_CONST:
-        return aw;
-    case HFS_OMEGA_SIN:
-        return aw * (1.0 + fabs(p.law[0]));
-    case HFS_OMEGA_COS_SQ:
-        return aw * sqrt(1.0 + fabs(p.law[0]));
-    case HFS_OMEGA_PULSE:
-        return aw * (1.0 + fabs(p.law[0]) * std::max(fabs(t0), fabs(t1)));
-    default:
-        return INFINITY;
-    }
+    double av[kMaxStages], bv[kMaxStages + 1];
+    int m = 0;
+    if (hfs::composition_fixed(comp, av, bv, &m)) return -1;
+    a.assign(av, av + m);
+    b.assign(bv, bv + m + 1);
+    return 0;
 }
 
 Layout make_layout(const hfs_ctx_s *c, int64_t chunk)

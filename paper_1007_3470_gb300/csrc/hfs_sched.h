@@ -71,4 +71,8 @@ cudaError_t launch_diag1d(bool fp64, const Diag1DArgs &a, int grid, cudaStream_t
 
 cudaError_t launch_twiddles(void *tw_f, void *tw_d, cudaStream_t st);
 
+// host helpers shared by the entry points (hfs_api.cu)
+int composition_fixed(int comp, double *a, double *b, int *m);
+double omega_bound(const hfs_instance &p, double t0, double t1);
+
 }  // namespace hfs

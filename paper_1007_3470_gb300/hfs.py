@@ -35,7 +35,7 @@ EXPORTS = ("hfs_create", "hfs_destroy", "hfs_set_stream", "hfs_state_size", "hfs
            "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_graphs",
            "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi", "hfs_step", "hfs_norm",
            "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_autotune", "hfs_set_profiling",
-           "hfs_last_step_kernel_ms", "hfs_error_string")
+           "hfs_last_step_kernel_ms", "hfs_step1d_noalloc", "hfs_error_string")
 
 
 class hfs_instance(ctypes.Structure):
@@ -95,6 +95,7 @@ def lib():
             "hfs_autotune": [vp, i32, ctypes.POINTER(ctypes.c_int32)],
             "hfs_set_profiling": [vp, i32],
             "hfs_last_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
+            "hfs_step1d_noalloc": [vp, i32, ctypes.POINTER(hfs_instance), i64, i32, i32, i32, dbl, dbl, i64, vp, i32],
             "hfs_error_string": [i32],
         }
         for name, args in sig.items():
@@ -257,6 +258,17 @@ def hfs_last_step_kernel_ms(h) -> float:
     ms = ctypes.c_float()
     _check(lib().hfs_last_step_kernel_ms(h, ctypes.byref(ms)), "hfs_last_step_kernel_ms")
     return ms.value
+
+
+NOALLOC_MAX_INSTANCES = 512
+
+
+def hfs_step1d_noalloc(psi_ptr: int, precision: int, instances: ctypes.Array, split: int, flow: int,
+                       composition: int, dt: float, t0: float, nsteps: int, stream_ptr: int = 0, wait: bool = True):
+    """Allocation-free batched 1D step on a caller-owned device state (see include/hfs.h)."""
+    _check(lib().hfs_step1d_noalloc(ctypes.c_void_p(psi_ptr), precision, instances, len(instances), split, flow,
+                                    composition, dt, t0, nsteps, ctypes.c_void_p(stream_ptr), 1 if wait else 0),
+           "hfs_step1d_noalloc")
 
 
 # --- convenience owner of the caller-side buffers ------------------------------
