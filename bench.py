@@ -71,7 +71,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -299,9 +299,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--cpu-sample", type=int, default=4, help="instances per grid size in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="instances per grid size in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
     ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
     args = ap.parse_args()

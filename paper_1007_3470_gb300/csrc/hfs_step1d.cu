@@ -52,8 +52,10 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
 constexpr int PHASE_GROUP = 4;
 template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
 {
+#ifndef HFS_NO_PHASE_FENCE
 #pragma unroll
     for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+f"(v[e].x), "+f"(v[e].y));
+#endif
 }
 template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E], int e0)
 {
@@ -152,7 +154,9 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         // integer and SFU operations) instead of holding 3E of them live
         // across the whole time loop.
         int tl = t;
+#ifndef HFS_NO_STEP_LAUNDER
         asm volatile("" : "+r"(tl));
+#endif
         xphase<N, E>(v, tl, rc, tp);
         FftPlan<N, E>::template run<false, R>(v, sm, tl, tw);
         kphase<N, E>(v, tl, rc);
@@ -173,9 +177,13 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     }
 }
 
+#ifdef HFS_ONLY_EPT8
+#define HFS_FOR_EACH_PLAN(X) X(2048, 8) X(1024, 8) X(512, 8) X(256, 8) X(128, 8)
+#else
 #define HFS_FOR_EACH_PLAN(X)                                                                                      \
     X(4096, 16) X(2048, 16) X(1024, 16) X(512, 16) X(256, 16) X(128, 16) X(2048, 8) X(1024, 8) X(512, 8)        \
         X(256, 8) X(128, 8)
+#endif
 
 // FP32: two CTAs per SM (128 registers); FP64 parity mode: one
 #ifndef HFS_STEP1D_MIN_CTAS
