@@ -108,6 +108,36 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank solves its own batch: the workload seed offset by the rank
+    (instances are independent, so the data path needs no communication)."""
+    from paper_1007_3470_gb300 import workloads as W
+    return W.SEED + rank
+
+
+def reduce_times_max(times, dist, device):
+    """Max over ranks of each timing (the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def reduce_sum(value: float, dist, device) -> float:
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t[0])
+
+
+def aggregate_value(gps_all_ranks: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the grid-point-steps of all ranks per solve, times
+    the timed solves, over the max-over-ranks timed span."""
+    return gps_all_ranks * steps / (total_ms * 1e-3)
+
+
 def algorithmic_counts(insts, steps):
     """Per solve: grid-point-steps, algorithmic flops and streaming bytes.
 
@@ -122,6 +152,62 @@ def algorithmic_counts(insts, steps):
     return gps, flops
 
 
+def extra_measurements(hfs, W, torch):
+    """Secondary measurements (not the headline): the 3D GPE step, the
+    streaming mode of the batched step (one launch, one global round trip
+    per time step), and single-instance vs batched solves at N = 256."""
+    out = {}
+
+    def kernel_ms(solver, nsteps, reps=2):
+        hfs.hfs_set_profiling(solver.h, True)
+        solver.step(nsteps)
+        best = 1e30
+        for _ in range(reps):
+            solver.step(nsteps)
+            best = min(best, hfs.hfs_last_step_kernel_ms(solver.h))
+        return best
+
+    # 3D, 128^3, sigma = 100, 200 Strang / Magnus-4 steps
+    inst, psi0, steps = W.gpe_3d(n=128, h=0.005, steps=200)
+    s3 = hfs.Solver([inst], dim=3, precision="c64", chunk_steps=steps)
+    s3.set_schedule(inst.h, "strang", hfs.HFS_FLOW_CF4)
+    s3.set_graphs(True)
+    s3.set_psi(psi0.ravel())
+    ms = kernel_ms(s3, steps)
+    gps = 128 ** 3 * steps
+    out["gpe3d_128cube_200steps_c64"] = {"kernel_ms": ms, "grid_point_steps_per_s": gps / (ms * 1e-3),
+                                         "hbm_equivalent_GBps_4_passes": gps * 64 / (ms * 1e-3) / 1e9}
+    s3.close()
+    # streaming mode of the batched workload (one launch per time step)
+    insts, psis, _ = W.batch_1d(count=COUNT, h=DT, steps=STEPS)
+    ss = hfs.Solver(insts, precision="c64", chunk_steps=STEPS)
+    ss.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    ss.set_mode(hfs.HFS_MODE_STREAMING, 1)
+    ss.set_graphs(True)
+    ss.set_psi(psis)
+    ms = kernel_ms(ss, STEPS)
+    gps = sum(i.n[0] for i in insts) * STEPS
+    out["batch_streaming_1step_per_launch"] = {"kernel_ms": ms, "grid_point_steps_per_s": gps / (ms * 1e-3),
+                                               "hbm_equivalent_GBps": gps * 16 / (ms * 1e-3) / 1e9}
+    ss.close()
+    # single instance vs batch at N = 256, 200 steps (T = 1)
+    one, p1, _ = W.batch_1d(count=4096, sizes=(256,), h=DT, steps=200)
+    s1 = hfs.Solver(one[:1], precision="c64", chunk_steps=200)
+    s1.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    s1.set_graphs(True)
+    s1.set_psi(p1[:1])
+    ms1 = kernel_ms(s1, 200)
+    s1.close()
+    sb = hfs.Solver(one, precision="c64", chunk_steps=200)
+    sb.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    sb.set_graphs(True)
+    sb.set_psi(p1)
+    msb = kernel_ms(sb, 200)
+    sb.close()
+    out["n256_T1_single_vs_batch"] = {"single_solves_per_s": 1e3 / ms1, "batch4096_solves_per_s": 4096e3 / msb}
+    return out
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -134,7 +220,7 @@ def run_native(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     COUNT_, STEPS_ = args.count, args.time_steps
-    insts, psis, _ = W.batch_1d(count=COUNT_, seed=W.SEED + rank, h=DT, steps=STEPS_)
+    insts, psis, _ = W.batch_1d(count=COUNT_, seed=rank_seed(rank), h=DT, steps=STEPS_)
     gps, flops = algorithmic_counts(insts, STEPS_)
     solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS_)
     solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
@@ -189,11 +275,9 @@ def run_native(args):
         hfs.hfs_get_psi(solver.h, pinned_out.data_ptr(), False)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step_ms = statistics.median(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms, e2e_step_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_step_ms = float(t[0]), float(t[1])
-    value = gps * ws * args.steps / (total_ms * 1e-3)
+    total_ms, e2e_step_ms = reduce_times_max([total_ms, e2e_step_ms], dist if ws > 1 else None, "cuda")
+    gps_all = reduce_sum(gps, dist if ws > 1 else None, "cuda")
+    value = aggregate_value(gps_all, args.steps, total_ms)
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -214,7 +298,7 @@ def run_native(args):
                      "frac": achieved_tflops / alu_peak, "traffic": None,
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz {src})",
                      "hbm_equivalent_GBps": hbm_equiv, "hbm_equivalent_frac_of_measured": hbm_equiv / hbm},
-        "e2e": {"value": gps * ws / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
+        "e2e": {"value": gps_all / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
                 "h2d_bytes_per_step": int(host0.nbytes), "d2h_bytes_per_step": int(host0.nbytes)},
         "gpu_launches": 4 * args.steps,
         "kernel_ms_per_launch": step_ms,
@@ -222,6 +306,8 @@ def run_native(args):
         "status": st,
         "wall_s": t_wall,
     }
+    if rank == 0 and not args.no_extras:
+        line["extras"] = extra_measurements(hfs, W, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     if rank == 0:
@@ -301,6 +387,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-sample", type=int, default=16, help="instances per grid size in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
