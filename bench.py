@@ -205,7 +205,39 @@ def extra_measurements(hfs, W, torch):
     msb = kernel_ms(sb, 200)
     sb.close()
     out["n256_T1_single_vs_batch"] = {"single_solves_per_s": 1e3 / ms1, "batch4096_solves_per_s": 4096e3 / msb}
+    out["surrogate_fno"] = surrogate_measurement()
     return out
+
+
+def surrogate_measurement():
+    """The FNO surrogate of the N = 256, T = 1 family: 20000 training and 2000
+    held-out solver trajectories, 30 epochs, held-out error distribution, and
+    its inference throughput (batch 4096) against the plain solver at the
+    surrogate's accuracy and at the reference step."""
+    import time
+    from paper_1007_3470_gb300 import surrogate as S
+    from paper_1007_3470_gb300.fno import Fno, FnoConfig
+    t0 = time.perf_counter()
+    tr_i, tr_p, _ = S.family(20000, seed=101)
+    te_i, te_p, _ = S.family(2000, seed=202)
+    Xtr, Xte = S.features(tr_i, tr_p), S.features(te_i, te_p)
+    Ytr, Yte = S.solve(tr_i, tr_p), S.solve(te_i, te_p)
+    t1 = time.perf_counter()
+    m = Fno(FnoConfig(), max_batch=4096, train=True, seed=7)
+    S.train(m, Xtr, Ytr, epochs=30, batch=256, lr=2e-3)
+    t2 = time.perf_counter()
+    err = S.rel_errors(S.predict(m, Xte, 4096), Yte)
+    med = float(np.median(err))
+    bi, bp, _ = S.family(4096, seed=303)
+    fno_rate = S.time_inference(m, S.features(bi, bp))
+    m.close()
+    dt, smed = S.equal_accuracy_solver(te_i, te_p, Yte, med)
+    return {"train_samples": 20000, "heldout": 2000, "epochs": 30, "data_s": t1 - t0, "train_s": t2 - t1,
+            "heldout_rel_l2": {"median": med, "p90": float(np.percentile(err, 90)), "max": float(err.max())},
+            "fno_solves_per_s_batch4096": fno_rate,
+            "solver_equal_accuracy": {"dt": dt, "median_rel_l2": smed,
+                                      "solves_per_s_batch4096": S.time_solver(bi, bp, dt)},
+            "solver_reference_dt_solves_per_s_batch4096": S.time_solver(bi, bp, S.DT)}
 
 
 def run_native(args):
