@@ -43,6 +43,32 @@ struct CS {
 __device__ CS cs_of(double w, double t)
 {
     CS r;
+    const double z = w * t * t;  // theta^2, negative for w < 0
+    if (fabs(z) <= 0.25) {
+        // Power series of the entire functions in z = w t^2 (Taylor series of
+        // cos and sin / theta), eight terms: truncation below 1e-18.  No square
+        // root, no division, and w <= 0 needs no separate branch.
+        double c = 1.0 / 20922789888000.0, s = 1.0 / 1307674368000.0, o = 1.0 / 20922789888000.0;
+        c = fma(c, -z, 1.0 / 87178291200.0);
+        c = fma(c, -z, 1.0 / 479001600.0);
+        c = fma(c, -z, 1.0 / 3628800.0);
+        c = fma(c, -z, 1.0 / 40320.0);
+        c = fma(c, -z, 1.0 / 720.0);
+        c = fma(c, -z, 1.0 / 24.0);
+        c = fma(c, -z, 1.0 / 2.0);  // (1 - C)/z
+        s = fma(s, -z, 1.0 / 6227020800.0);
+        s = fma(s, -z, 1.0 / 39916800.0);
+        s = fma(s, -z, 1.0 / 362880.0);
+        s = fma(s, -z, 1.0 / 5040.0);
+        s = fma(s, -z, 1.0 / 120.0);
+        s = fma(s, -z, 1.0 / 6.0);
+        s = fma(s, -z, 1.0);  // S / t
+        (void)o;
+        r.OMC = z * c;
+        r.C = 1.0 - r.OMC;
+        r.S = t * s;
+        return r;
+    }
     if (w > 0.0) {
         const double q = sqrt(w);
         double sh, ch;
@@ -50,16 +76,12 @@ __device__ CS cs_of(double w, double t)
         r.C = 1.0 - 2.0 * sh * sh;
         r.OMC = 2.0 * sh * sh;
         r.S = 2.0 * sh * ch / q;
-    } else if (w < 0.0) {
+    } else {
         const double q = sqrt(-w);
         const double sh = sinh(0.5 * q * t), ch = cosh(0.5 * q * t);
         r.C = 1.0 + 2.0 * sh * sh;
         r.OMC = -2.0 * sh * sh;
         r.S = 2.0 * sh * ch / q;
-    } else {
-        r.C = 1.0;
-        r.OMC = 0.0;
-        r.S = t;
     }
     return r;
 }
@@ -179,6 +201,8 @@ __device__ __forceinline__ void split_hi_lo(double v, float &hi, float &lo)
 __device__ __forceinline__ double frac1(double v) { return v - rint(v); }
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
+constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
 
 // one thread per (instance, sub-stage j in [0, nstage]) -- 1D records
 template <typename RecT>
@@ -195,11 +219,11 @@ __global__ void records1d_kernel(const DevInst *__restrict__ inst, int64_t count
     const double t0 = *t_dev + t_off;
     double kappa, bs, g;
     merged_coeffs(p, 1, 0, sc, t0, j, nstage, fge + i * nstage, kappa, bs, g);
-    const double K2 = kappa * p.dx[0] * p.dx[0] / (4.0 * kPi);
-    const double K1 = kappa * p.xc[0] * p.dx[0] / (2.0 * kPi);
-    const double K0 = frac1(kappa * p.xc[0] * p.xc[0] / (4.0 * kPi));
+    const double K2 = kappa * p.dx[0] * p.dx[0] * kInv4Pi;
+    const double K1 = kappa * p.xc[0] * p.dx[0] * kInv2Pi;
+    const double K0 = frac1(kappa * p.xc[0] * p.xc[0] * kInv4Pi);
     const double G = g * kPi / (p.len[0] * p.len[0]);
-    const double SB = bs * sc.h / (2.0 * kPi);
+    const double SB = bs * sc.h * kInv2Pi;
     if (!isfinite(K2) || !isfinite(G) || !isfinite(K1)) atomicOr(status, (unsigned)ST_NONFINITE);
     RecT r;
     if constexpr (sizeof(RecT) == sizeof(RecF)) {
