@@ -378,6 +378,52 @@ def cpu_baseline(per_size: int):
                       f"FP64 stage-by-stage oracle, {dt:.1f} s"}
 
 
+def run_case(args):
+    """One secondary workload alone (for profiling): 3d | fno | streaming."""
+    import torch
+    from paper_1007_3470_gb300 import hfs
+    from paper_1007_3470_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    if args.case == "3d":
+        inst, psi0, steps = W.gpe_3d(n=128, h=0.005, steps=args.time_steps)
+        s3 = hfs.Solver([inst], dim=3, precision="c64", chunk_steps=steps)
+        s3.set_schedule(inst.h, "strang", hfs.HFS_FLOW_CF4)
+        hfs.hfs_set_profiling(s3.h, True)
+        s3.set_psi(psi0.ravel())
+        for _ in range(args.warmup):
+            s3.step(steps)
+        ms = []
+        for _ in range(args.steps):
+            s3.step(steps)
+            ms.append(hfs.hfs_last_step_kernel_ms(s3.h))
+        s3.close()
+        print(json.dumps({"case": "3d", "n": 128, "time_steps": steps, "kernel_ms": ms,
+                          "grid_point_steps_per_s": 128 ** 3 * steps / (min(ms) * 1e-3)}))
+    elif args.case == "fno":
+        from paper_1007_3470_gb300 import surrogate as S
+        from paper_1007_3470_gb300.fno import Fno, FnoConfig
+        bi, bp, _ = S.family(args.count, seed=303)
+        X = S.features(bi, bp)
+        Y = S.solve(bi, bp)
+        m = Fno(FnoConfig(), max_batch=args.count, train=True, seed=7)
+        xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            m.train_step(xd, yd, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            m.train_step(xd, yd, 1e-3, want_loss=False)
+        m.stream.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        rate = S.time_inference(m, X)
+        m.close()
+        print(json.dumps({"case": "fno", "batch": args.count, "train_step_ms": dt * 1e3,
+                          "inference_samples_per_s": rate}))
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -424,7 +470,14 @@ def main():
                     help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
     ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
+    ap.add_argument("--case", choices=["3d", "fno"], default=None,
+                    help="run one secondary workload alone (profiling)")
     args = ap.parse_args()
+    if args.case:
+        from paper_1007_3470_gb300 import build as B
+        B.build()
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -166,6 +166,9 @@ cudaError_t run(const GemmArgs &g, bool ta, bool tb, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// row-split of the column sums: about 64 rows per block
+inline unsigned colsum_blocks(int64_t rows) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(4096, rows / 64)); }
+
 // split-K weight gradient dW (+)= A^T B over `rows` (both row-major, K = rows)
 cudaError_t weight_grad(int M, int N, int64_t rows, const bf16 *A, int64_t lda, const bf16 *B, int64_t ldb, float *dW,
                         cudaStream_t st)
@@ -322,13 +325,13 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
     bf16 *dOb = at<bf16>(f, w.dOb);
     loss_sums_kernel<<<B, 256, 0, st>>>(O, y, L * OC, sums);
     loss_grad_kernel<<<blocks(rows * OC), 256, 0, st>>>(O, y, sums, L * OC, B, dO, dOb);
-    loss_value_kernel<<<1, 32, 0, st>>>(sums, B, at<float>(f, w.loss));
+    loss_value_kernel<<<1, 256, 0, st>>>(sums, B, at<float>(f, w.loss));
     FCK(cudaGetLastError());
     // projection
     bf16 *Qb = at<bf16>(f, w.Qb), *dQb = at<bf16>(f, w.dQb);
     float *dQ = at<float>(f, w.dQ);
     FCK(weight_grad((int)P, (int)OC, rows, Qb, P, dOb, OC, grad + f->po.P2, st));
-    colsum_kernel<<<64, (unsigned)OC, 0, st>>>(dO, rows, (int)OC, grad + f->po.c2);
+    colsum_kernel<<<colsum_blocks(rows), (unsigned)OC, 0, st>>>(dO, rows, (int)OC, grad + f->po.c2);
     {
         GemmArgs g = gemm((int)rows, (int)P, (int)OC, dOb, OC, at<bf16>(f, w.P2b), OC);  // dQ = dO P2^T
         g.C = dQ;
@@ -338,7 +341,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
     gelu_bwd_kernel<<<blocks(rows * P), 256, 0, st>>>(dQ, at<float>(f, w.Qpre), 1, dQ, dQb, rows * P);
     bf16 *Hb = at<bf16>(f, w.Hb);
     FCK(weight_grad((int)C, (int)P, rows, Hb + NL * rowsM * C, C, dQb, P, grad + f->po.P1, st));
-    colsum_kernel<<<64, (unsigned)P, 0, st>>>(dQ, rows, (int)P, grad + f->po.c1);
+    colsum_kernel<<<colsum_blocks(rows), (unsigned)P, 0, st>>>(dQ, rows, (int)P, grad + f->po.c1);
     float *dH = at<float>(f, w.dH), *dZ = at<float>(f, w.dZ);
     bf16 *dZb = at<bf16>(f, w.dZb);
     {
@@ -354,7 +357,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
                                                           (l < NL - 1) ? 1 : 0, dZ, dZb, rows * C);
         const bf16 *Hinb = Hb + l * rowsM * C;
         FCK(weight_grad((int)C, (int)C, rows, Hinb, C, dZb, C, grad + f->po.W[l], st));
-        colsum_kernel<<<64, (unsigned)C, 0, st>>>(dZ, rows, (int)C, grad + f->po.b[l]);
+        colsum_kernel<<<colsum_blocks(rows), (unsigned)C, 0, st>>>(dZ, rows, (int)C, grad + f->po.b[l]);
         {
             GemmArgs g = gemm((int)rows, (int)C, (int)C, dZb, C, at<bf16>(f, w.Wb) + l * C * C, C);  // dZ W^T
             g.C = dH;
@@ -414,7 +417,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
     // dP_in over the padded input rows into scratch, then keep the first in_ch rows
     FCK(cudaMemsetAsync(at<float>(f, w.dR1), 0, 4 * kInPad * C, st));
     FCK(weight_grad(kInPad, (int)C, rows, at<bf16>(f, w.X8), kInPad, dZb, C, at<float>(f, w.dR1), st));
-    colsum_kernel<<<64, (unsigned)C, 0, st>>>(dH, rows, (int)C, grad + f->po.bin);
+    colsum_kernel<<<colsum_blocks(rows), (unsigned)C, 0, st>>>(dH, rows, (int)C, grad + f->po.bin);
     FCK(cudaMemcpyAsync(grad + f->po.Pin, at<float>(f, w.dR1), 4 * c.in_ch * C, cudaMemcpyDeviceToDevice, st));
     FCK(cudaGetLastError());
     return HFS_OK;

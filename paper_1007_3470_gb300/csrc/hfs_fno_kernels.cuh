@@ -248,12 +248,19 @@ __global__ void loss_grad_kernel(const float *O, const float *Y, const float *su
     dOb[i] = __float2bfloat16(v);
 }
 
+// one block of 256 threads
 __global__ void loss_value_kernel(const float *sums, int batch, float *loss)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int b = 0; b < batch; ++b) s += sqrt((double)sums[2 * b] / (double)sums[2 * b + 1]);
-    *loss = (float)(s / batch);
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) s += sqrtf(sums[2 * b] / sums[2 * b + 1]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / (float)batch;
 }
 
 __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,

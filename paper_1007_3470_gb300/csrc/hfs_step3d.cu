@@ -149,6 +149,100 @@ template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpas
 }
 
 // ---------------------------------------------------------------------------
+// plane pass (complex64, n = 128): one CTA owns a whole z-plane in shared
+// memory (rows y of 128 + 8 padded slots) and runs, as the mode asks,
+//   inverse FFT_y -> [inverse FFT_x, x-phase, forward FFT_x] -> forward FFT_y
+// so that a sub-stage costs this pass plus the z-pass: two global round
+// trips instead of four.  512 threads: 64 lines of 8 threads per round.
+// ---------------------------------------------------------------------------
+enum : int { P_INV_Y = 1, P_INV_X = 2, P_PHASE = 4, P_FWD_X = 8, P_FWD_Y = 16 };
+constexpr int kPlaneN = 128, kPlaneRow = kPlaneN + kPlaneN / 16, kPlaneThreads = 512;
+
+template <int MODE> __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, int64_t j)
+{
+    constexpr int N = kPlaneN, E = 16, T = N / E, LINES = kPlaneThreads / T;  // 64 lines per round
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float> *pl = reinterpret_cast<cpx<float> *>(smem_raw);
+    const int z = blockIdx.x;
+    cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
+    const auto *tw = reinterpret_cast<const float4 *>(a.tw) + twiddle_offset(N);
+    // load the plane: element (y, x) -> row y, padded slot of x
+    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) pl[(i / N) * kPlaneRow + spad(i % N)] = psi[i];
+    __syncthreads();
+    cpx<float> v[E];
+    if constexpr (MODE & P_INV_Y) {
+        // columns: lanes are adjacent x, slots of a column are kPlaneRow apart
+        const int l = threadIdx.x % LINES, t = threadIdx.x / LINES;
+        for (int r = 0; r < N / LINES; ++r) {
+            cpx<float> *col = pl + spad(r * LINES + l);
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = col[(t + T * e) * kPlaneRow];
+            __syncthreads();
+            FftPlan<N, E>::template run<true, float, kPlaneRow>(v, col, t, tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) col[(t + T * e) * kPlaneRow] = v[e];
+            __syncthreads();
+        }
+    }
+    if constexpr ((MODE & P_INV_X) || (MODE & P_PHASE) || (MODE & P_FWD_X)) {
+        const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+        const DevInst &ip = *a.inst;
+        const Rec3F rc = reinterpret_cast<const Rec3F *>(a.rec)[j];
+        const int mz = z - N / 2;
+        const int vkind = (ip.eps != 0.0) ? ip.vi_kind : HFS_VI_NONE;
+        const float dx = (float)ip.dx[0], vk = (float)ip.vi_k, eps = (float)ip.eps, sig = (float)ip.sigma;
+        const float tz = turns_q(mz, rc.k2[2], rc.k2lo[2]);
+        const float vz = vi_eval(vkind, (float)mz * (float)ip.dx[2], vk);
+        for (int r = 0; r < N / LINES; ++r) {
+            const int y = r * LINES + g;
+            cpx<float> *row = pl + y * kPlaneRow;
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = row[spad(t + T * e)];
+            __syncthreads();
+            if constexpr (MODE & P_INV_X) FftPlan<N, E>::template run<true, float>(v, row, t, tw);
+            if constexpr (MODE & P_PHASE) {
+                const int my = y - N / 2;
+                const float tyz = turns_q(my, rc.k2[1], rc.k2lo[1]) + tz;
+                const float vyz = vi_eval(vkind, (float)my * (float)ip.dx[1], vk) + vz;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int mx = t + T * e - N / 2;
+                    float turns = turns_q(mx, rc.k2[0], rc.k2lo[0]) + tyz;
+                    const float dens = v[e].x * v[e].x + v[e].y * v[e].y;
+                    const float F = sig * dens + eps * (vi_eval(vkind, (float)mx * dx, vk) + vyz);
+                    turns += rc.sb2pi * F;
+                    v[e] = apply_turns(v[e], turns, 1.0f);
+                }
+            }
+            if constexpr (MODE & P_FWD_X) FftPlan<N, E>::template run<false, float>(v, row, t, tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) row[spad(t + T * e)] = v[e];
+            __syncthreads();
+        }
+    }
+    if constexpr (MODE & P_FWD_Y) {
+        const int l = threadIdx.x % LINES, t = threadIdx.x / LINES;
+        for (int r = 0; r < N / LINES; ++r) {
+            cpx<float> *col = pl + spad(r * LINES + l);
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = col[(t + T * e) * kPlaneRow];
+            __syncthreads();
+            FftPlan<N, E>::template run<false, float, kPlaneRow>(v, col, t, tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) col[(t + T * e) * kPlaneRow] = v[e];
+            __syncthreads();
+        }
+    }
+    bool bad = false;
+    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
+        const cpx<float> w = pl[(i / N) * kPlaneRow + spad(i % N)];
+        psi[i] = w;
+        bad |= !(isfinite(w.x) && isfinite(w.y));
+    }
+    if ((MODE & P_PHASE) && !(MODE & P_FWD_X) && bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
 // diagnostics: norm, potential + interaction, and the kinetic energy as a sum
 // over axes of 1D Parseval sums  sum_x |d_d u|^2 = (1/n) sum_k k_d^2 |F_d u|^2
 // ---------------------------------------------------------------------------
@@ -314,8 +408,35 @@ template <typename R, int N> static cudaError_t diag3d(const Diag3DArgs &a, cuda
     return cudaGetLastError();
 }
 
+static cudaError_t run3d_plane(const Step3DArgs &a, cudaStream_t st)
+{
+    constexpr int N = kPlaneN;
+    using GEO = Geo3<N>;
+    const size_t ps = (size_t)N * kPlaneRow * sizeof(cpx<float>), ts = tsmem<float, N>();
+    static bool prepared = false;
+    if (!prepared) {
+        cudaError_t e;
+        if ((e = allow_smem(plane3d<P_PHASE | P_FWD_X | P_FWD_Y>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<P_INV_Y | P_INV_X | P_PHASE | P_FWD_X | P_FWD_Y>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<P_INV_Y | P_INV_X | P_PHASE>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(zpass3d<float, N>, ts)) != cudaSuccess) return e;
+        prepared = true;
+    }
+    const dim3 tg(N / GEO::TX, N);
+    plane3d<P_PHASE | P_FWD_X | P_FWD_Y><<<N, kPlaneThreads, ps, st>>>(a, 0);
+    for (int64_t j = 0; j < a.nstage; ++j) {
+        zpass3d<float, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        if (j + 1 < a.nstage)
+            plane3d<P_INV_Y | P_INV_X | P_PHASE | P_FWD_X | P_FWD_Y><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+        else
+            plane3d<P_INV_Y | P_INV_X | P_PHASE><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step3d(bool fp64, const Step3DArgs &a, cudaStream_t st)
 {
+    if (!fp64 && a.n == kPlaneN) return run3d_plane(a, st);
     switch (a.n) {
     case 32: return fp64 ? run3d<double, 32>(a, st) : run3d<float, 32>(a, st);
     case 64: return fp64 ? run3d<double, 64>(a, st) : run3d<float, 64>(a, st);
