@@ -43,6 +43,31 @@ METRIC = "grid-point-steps/s"
 COUNT, STEPS, DT = 4096, 500, 0.005
 
 
+# DRAM bytes per launch of the fused step kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the same command, summarised in
+# profiles/), valid only while the kernel's sources hash to "src".
+STEP1D_TRAFFIC = {"src": "58b5a2b8aee2290a",
+                  "batch_1d_4096x500_c64": 111118592 + 627253248,
+                  "batch_1d_65536x1_streaming": (731394816 + 1070601984 + 731420672 + 1064741888) // 2}
+STEP1D_SOURCES = ("hfs_step1d.cu", "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_law.cuh", "hfs_sched.h")
+
+
+def step1d_traffic(workload: str):
+    """Captured DRAM bytes per launch for this workload, or None when the
+    kernel sources changed since the capture (or the workload was not captured)."""
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in STEP1D_SOURCES:
+            with open(os.path.join(ROOT, "paper_1007_3470_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    if h.hexdigest()[:16] != STEP1D_TRAFFIC["src"]:
+        return None
+    return STEP1D_TRAFFIC.get(workload)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -205,8 +230,38 @@ def extra_measurements(hfs, W, torch):
     msb = kernel_ms(sb, 200)
     sb.close()
     out["n256_T1_single_vs_batch"] = {"single_solves_per_s": 1e3 / ms1, "batch4096_solves_per_s": 4096e3 / msb}
+    out["batch65536_streaming_hbm"] = hbm_streaming_measurement(hfs, W)
     out["surrogate_fno"] = surrogate_measurement()
     return out
+
+
+def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
+    """The streaming mode on a batch whose state exceeds L2: 65536 instances
+    of the same law (about 700 MB complex64), one launch per time step, so
+    every launch reads and writes the whole state in HBM."""
+    insts, psis, _ = W.batch_1d(count=count, seed=W.SEED + 65536, h=DT, steps=steps)
+    pts = sum(i.n[0] for i in insts)
+    s = hfs.Solver(insts, precision="c64", chunk_steps=steps)
+    s.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    s.set_mode(hfs.HFS_MODE_STREAMING, 1)
+    s.set_graphs(True)
+    hfs.hfs_set_profiling(s.h, True)
+    s.set_psi(psis)
+    s.step(steps)
+    best = 1e30
+    for _ in range(2):
+        s.step(steps)
+        best = min(best, hfs.hfs_last_step_kernel_ms(s.h))
+    st = s.status()
+    s.close()
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbps = pts * steps * 16.0 / (best * 1e-3) / 1e9
+    traffic = step1d_traffic("batch_1d_65536x1_streaming") if count == 65536 else None
+    return {"instances": count, "points": pts, "state_MB": pts * 8 / 1e6, "time_steps": steps,
+            "ms_per_launch": best / steps, "grid_point_steps_per_s": pts * steps / (best * 1e-3),
+            "hbm_GBps_algorithmic": gbps, "hbm_frac_of_measured": gbps / hbm,
+            "algorithmic_bytes_per_launch": pts * 16, "dram_bytes_per_launch": traffic, "status": st}
 
 
 def surrogate_measurement():
@@ -317,17 +372,20 @@ def run_native(args):
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     achieved_tflops = flops / (step_ms * 1e-3) / 1e12
     hbm_equiv = gps * 16.0 / (step_ms * 1e-3) / 1e9
+    workload = f"batch_1d_{COUNT_}x{STEPS_}_c64"
     line = {
         "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
-        "config": {"workload": f"batch_1d_{COUNT_}x{STEPS_}_c64", "instances": COUNT_, "time_steps": STEPS_,
+        "config": {"workload": workload, "instances": COUNT_, "time_steps": STEPS_,
                    "dt": DT, "grid_sizes": "128..4096 uniform", "composition": "strang", "ho_flow": "magnus4_cf+thm2",
                    "mode": "resident, graph-replayed", "l2": "flushed between steps (256 MiB write)",
                    "solves_per_s": ws * args.steps / (total_ms * 1e-3),
                    "plans_ept": tuned},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / alu_peak, "traffic": None,
+                     "frac": achieved_tflops / alu_peak, "traffic": step1d_traffic(workload),
+                     "traffic_note": "DRAM bytes per launch (ncu); the state stays on chip for all time "
+                                     "steps, the rest is schedule records and spill write-back",
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz {src})",
                      "hbm_equivalent_GBps": hbm_equiv, "hbm_equivalent_frac_of_measured": hbm_equiv / hbm},
         "e2e": {"value": gps_all / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
@@ -379,7 +437,8 @@ def cpu_baseline(per_size: int):
 
 
 def run_case(args):
-    """One secondary workload alone (for profiling): 3d | fno | streaming."""
+    """One secondary workload alone (for profiling): 3d | fno | hbm (streaming
+    mode on a batch larger than L2)."""
     import torch
     from paper_1007_3470_gb300 import hfs
     from paper_1007_3470_gb300 import workloads as W
@@ -420,6 +479,9 @@ def run_case(args):
         m.close()
         print(json.dumps({"case": "fno", "batch": args.count, "train_step_ms": dt * 1e3,
                           "inference_samples_per_s": rate}))
+    elif args.case == "hbm":
+        print(json.dumps({"case": "hbm", **hbm_streaming_measurement(hfs, W, count=args.count,
+                                                                     steps=args.time_steps)}))
     else:
         raise SystemExit(f"unknown case {args.case}")
 
@@ -443,6 +505,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = gps * args.steps / total
+    workload = f"batch_1d_{COUNT_}x{STEPS_}_c64"
     line = {
         "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -470,7 +533,7 @@ def main():
                     help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
     ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
-    ap.add_argument("--case", choices=["3d", "fno"], default=None,
+    ap.add_argument("--case", choices=["3d", "fno", "hbm"], default=None,
                     help="run one secondary workload alone (profiling)")
     args = ap.parse_args()
     if args.case:

@@ -122,6 +122,13 @@ def test_modes_graphs_and_plans_agree():
     for a, b in zip(base, alt):
         assert O.rel_l2(b, a) < 5e-6
     s.close()
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    assert max(O.rel_l2(b, r) for b, r in zip(alt, refs)) <= budget(TOL_C64, steps * 0.005)
+    # a 4096-point instance with 8 values per thread would need a 512-thread team
+    d = hfs.Solver(insts[:2], precision="c64")
+    with pytest.raises(RuntimeError):
+        d.set_plan(4096, 8)
+    d.close()
 
 
 def test_graph_replay_advances_time():
