@@ -226,7 +226,6 @@ int forward(hfs_fno_s *f, const float *x, int B)
         FCK(run(g, false, false, st));
     }
     for (int l = 0; l < NL; ++l) {
-        const float *Hin = Hf + l * rowsM * C;
         const bf16 *Hinb = Hb + l * rowsM * C;
         bf16 *S = at<bf16>(f, w.S) + l * Bm * 2 * M * C;
         // S_b = F2 H_b   (2M x C per sample)
@@ -289,7 +288,6 @@ int forward(hfs_fno_s *f, const float *x, int B)
             g.ldcb = C;
             FCK(run(g, false, false, st));
         }
-        (void)Hin;
     }
     // projection: Q = GELU(H P1 + c1); O = Q P2 + c2
     {

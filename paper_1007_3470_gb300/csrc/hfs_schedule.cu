@@ -48,7 +48,7 @@ __device__ CS cs_of(double w, double t)
         // Power series of the entire functions in z = w t^2 (Taylor series of
         // cos and sin / theta), eight terms: truncation below 1e-18.  No square
         // root, no division, and w <= 0 needs no separate branch.
-        double c = 1.0 / 20922789888000.0, s = 1.0 / 1307674368000.0, o = 1.0 / 20922789888000.0;
+        double c = 1.0 / 20922789888000.0, s = 1.0 / 1307674368000.0;
         c = fma(c, -z, 1.0 / 87178291200.0);
         c = fma(c, -z, 1.0 / 479001600.0);
         c = fma(c, -z, 1.0 / 3628800.0);
