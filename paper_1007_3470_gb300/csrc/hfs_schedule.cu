@@ -63,7 +63,6 @@ __device__ CS cs_of(double w, double t)
         s = fma(s, -z, 1.0 / 120.0);
         s = fma(s, -z, 1.0 / 6.0);
         s = fma(s, -z, 1.0);  // S / t
-        (void)o;
         r.OMC = z * c;
         r.C = 1.0 - r.OMC;
         r.S = t * s;
