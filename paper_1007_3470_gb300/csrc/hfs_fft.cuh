@@ -102,6 +102,33 @@ __device__ __forceinline__ void dft4(cpx<R> &a0, cpx<R> &a1, cpx<R> &a2, cpx<R> 
     a3 = csub(t1, t3);
 }
 
+// FP32 radix-4 in packed two-lane instructions; the multiplication by -+i
+// folds into the last two.  Bit-identical to dft4<INV, float>.
+template <bool INV>
+__device__ __forceinline__ void dft4p(cpx<float> &a0, cpx<float> &a1, cpx<float> &a2, cpx<float> &a3)
+{
+    const cpx<float> t0 = cadd_p(a0, a2), t1 = csub_p(a0, a2);
+    const cpx<float> t2 = cadd_p(a1, a3), d = csub_p(a1, a3);
+    a0 = cadd_p(t0, t2);
+    a2 = csub_p(t0, t2);
+    a1 = cadd_rot_p<INV ? -1 : 1>(t1, d);
+    a3 = cadd_rot_p<INV ? 1 : -1>(t1, d);
+}
+// Radix-4 stage of the radix-16 and radix-8 butterflies: packed in FP32
+// where that measured faster (radix 16).
+#ifndef HFS_PACK_DFT16
+#define HFS_PACK_DFT16 1
+#endif
+#ifndef HFS_PACK_DFT8
+#define HFS_PACK_DFT8 0
+#endif
+template <bool INV, bool PACK, typename R>
+__device__ __forceinline__ void dft4s(cpx<R> &a0, cpx<R> &a1, cpx<R> &a2, cpx<R> &a3)
+{
+    if constexpr (PACK && sizeof(R) == 4) dft4p<INV>(a0, a1, a2, a3);
+    else dft4<INV>(a0, a1, a2, a3);
+}
+
 template <bool INV, typename R> __device__ __forceinline__ void dft4v(cpx<R> *a) { dft4<INV>(a[0], a[1], a[2], a[3]); }
 
 // radix 8 = 2 x 4: even/odd radix-4 transforms combined with W_8^k
@@ -109,8 +136,8 @@ template <bool INV, typename R> __device__ __forceinline__ void dft8v(cpx<R> *a)
 {
     cpx<R> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
     cpx<R> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
-    dft4<INV>(e0, e1, e2, e3);
-    dft4<INV>(o0, o1, o2, o3);
+    dft4s<INV, HFS_PACK_DFT8 != 0>(e0, e1, e2, e3);
+    dft4s<INV, HFS_PACK_DFT8 != 0>(o0, o1, o2, o3);
     o1 = rot16<2, INV>(o1);
     o2 = rot16<4, INV>(o2);
     o3 = rot16<6, INV>(o3);
@@ -128,10 +155,10 @@ template <bool INV, typename R> __device__ __forceinline__ void dft8v(cpx<R> *a)
 template <bool INV, typename R> __device__ __forceinline__ void dft16v(cpx<R> *a)
 {
     // inner radix-4 over j2 for each j1 -> b[j1][k1] stored at a[j1 + 4 j2] with j2 := k1
-    dft4<INV>(a[0], a[4], a[8], a[12]);
-    dft4<INV>(a[1], a[5], a[9], a[13]);
-    dft4<INV>(a[2], a[6], a[10], a[14]);
-    dft4<INV>(a[3], a[7], a[11], a[15]);
+    dft4s<INV, HFS_PACK_DFT16 != 0>(a[0], a[4], a[8], a[12]);
+    dft4s<INV, HFS_PACK_DFT16 != 0>(a[1], a[5], a[9], a[13]);
+    dft4s<INV, HFS_PACK_DFT16 != 0>(a[2], a[6], a[10], a[14]);
+    dft4s<INV, HFS_PACK_DFT16 != 0>(a[3], a[7], a[11], a[15]);
     // twiddles W_16^{j1 k1}: element a[j1 + 4 k1]
     a[5] = rot16<1, INV>(a[5]);
     a[9] = rot16<2, INV>(a[9]);
@@ -147,7 +174,7 @@ template <bool INV, typename R> __device__ __forceinline__ void dft16v(cpx<R> *a
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
         cpx<R> b0 = a[4 * k1 + 0], b1 = a[4 * k1 + 1], b2 = a[4 * k1 + 2], b3 = a[4 * k1 + 3];
-        dft4<INV>(b0, b1, b2, b3);
+        dft4s<INV, HFS_PACK_DFT16 != 0>(b0, b1, b2, b3);
         x[k1 + 0] = b0;
         x[k1 + 4] = b1;
         x[k1 + 8] = b2;

@@ -18,6 +18,35 @@ template <typename R> struct alignas(2 * sizeof(R)) cpx {
 
 template <typename R> __device__ __forceinline__ cpx<R> cadd(cpx<R> a, cpx<R> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename R> __device__ __forceinline__ cpx<R> csub(cpx<R> a, cpx<R> b) { return {a.x - b.x, a.y - b.y}; }
+
+// Packed FP32 complex add / subtract (one two-lane instruction, sm_100
+// family).  Each lane is the same IEEE round-to-nearest operation as the
+// scalar form, so results are bit-identical to cadd / csub.
+#ifndef HFS_PACK_SUBNEG
+#define HFS_PACK_SUBNEG 1
+#endif
+__device__ __forceinline__ float2 f2(cpx<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ cpx<float> cadd_p(cpx<float> a, cpx<float> b)
+{
+    const float2 r = __fadd2_rn(f2(a), f2(b));
+    return {r.x, r.y};
+}
+__device__ __forceinline__ cpx<float> csub_p(cpx<float> a, cpx<float> b)
+{
+#if HFS_PACK_SUBNEG
+    const float2 r = __fadd2_rn(f2(a), make_float2(-b.x, -b.y));
+#else
+    const float2 r = __ffma2_rn(f2(b), make_float2(-1.0f, -1.0f), f2(a));  // exact product
+#endif
+    return {r.x, r.y};
+}
+// t + SG (-i) d = (t.x + SG d.y, t.y - SG d.x), SG = +-1, as one packed fma
+template <int SG> __device__ __forceinline__ cpx<float> cadd_rot_p(cpx<float> t, cpx<float> d)
+{
+    const float2 r = __ffma2_rn(make_float2(d.y, d.x), make_float2((float)SG, (float)-SG), f2(t));
+    return {r.x, r.y};
+}
+
 template <typename R> __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b)
 {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};

@@ -65,6 +65,72 @@ __device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, flo
     return {ox * scale, oy * scale};
 }
 
+// Two grid points at once: the same per-lane operations as frac_turns /
+// apply_turns above; with PK the FP32 arithmetic runs in packed two-lane
+// instructions (sm_100 family), so the results are bit-identical either way.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 rint2(float2 a) { return make_float2(rintf(a.x), rintf(a.y)); }
+__device__ __forceinline__ float2 bc2(float c) { return make_float2(c, c); }
+
+template <bool PK> __device__ __forceinline__ float2 frac_turns2(float2 m2, float hi, float lo)
+{
+    if constexpr (PK) {
+        const float2 p = __fmul2_rn(bc2(hi), m2);
+        const float2 err = __ffma2_rn(bc2(hi), m2, neg2(p));
+        const float2 r = __fadd2_rn(p, neg2(rint2(p)));
+        return __fadd2_rn(r, __ffma2_rn(bc2(lo), m2, err));
+    } else {
+        return make_float2(frac_turns(m2.x, hi, lo), frac_turns(m2.y, hi, lo));
+    }
+}
+
+// the small-rotation part of apply_turns for two points: quarter turns q,
+// sin theta and cos theta - 1
+__device__ __forceinline__ void small_rotation2(float2 turns, float2 &q, float2 &sn, float2 &cm1)
+{
+    const float2 r = __fadd2_rn(turns, neg2(rint2(turns)));
+    q = rint2(__fmul2_rn(bc2(4.0f), r));
+    const float2 f = __ffma2_rn(q, bc2(-0.25f), r);
+    const float2 th = __fmul2_rn(f, bc2(6.28318530717958647692f));
+    const float2 t2 = __fmul2_rn(th, th);
+    float2 ps = __ffma2_rn(t2, bc2(1.0f / 362880.0f), bc2(-1.0f / 5040.0f));
+    ps = __ffma2_rn(ps, t2, bc2(1.0f / 120.0f));
+    ps = __ffma2_rn(ps, t2, bc2(-1.0f / 6.0f));
+    sn = __ffma2_rn(__fmul2_rn(th, t2), ps, th);
+    float2 pc = __ffma2_rn(t2, bc2(-1.0f / 3628800.0f), bc2(1.0f / 40320.0f));
+    pc = __ffma2_rn(pc, t2, bc2(-1.0f / 720.0f));
+    pc = __ffma2_rn(pc, t2, bc2(1.0f / 24.0f));
+    pc = __ffma2_rn(pc, t2, bc2(-0.5f));
+    cm1 = __fmul2_rn(t2, pc);
+}
+
+// u (1 + cm1 - i sn) followed by the exact quarter turn (-i)^q and the scale
+__device__ __forceinline__ cpx<float> finish_rotation(cpx<float> u, float q, float sn, float cm1, float scale)
+{
+    const float wx = u.x + fmaf(u.x, cm1, u.y * sn);
+    const float wy = u.y + fmaf(u.y, cm1, -u.x * sn);
+    const int qi = ((int)q) & 3;
+    float ox = (qi & 1) ? wy : wx;
+    float oy = (qi & 1) ? wx : wy;
+    ox = (qi >= 2) ? -ox : ox;
+    oy = (qi == 1 || qi == 2) ? -oy : oy;
+    return {ox * scale, oy * scale};
+}
+
+template <bool PK>
+__device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, float2 turns, float scale)
+{
+    if constexpr (PK) {
+        float2 q, sn, cm1;
+        small_rotation2(turns, q, sn, cm1);
+        u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
+        u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
+    } else {
+        u0 = apply_turns(u0, turns.x, scale);
+        u1 = apply_turns(u1, turns.y, scale);
+    }
+}
+
 __device__ __forceinline__ cpx<double> apply_turns(cpx<double> u, double turns, double scale)
 {
     turns -= rint(turns);

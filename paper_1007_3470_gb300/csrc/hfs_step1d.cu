@@ -49,7 +49,16 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
 // Opaque dependence on a group of register values: work on later groups
 // cannot be scheduled before this point, so the phase loops below keep one
 // group of PHASE_GROUP elements in flight instead of interleaving all E.
-constexpr int PHASE_GROUP = 4;
+#ifndef HFS_PHASE_GROUP
+#define HFS_PHASE_GROUP 4
+#endif
+constexpr int PHASE_GROUP = HFS_PHASE_GROUP;
+// Phase arithmetic of point pairs in packed FP32 instructions for plans with
+// at least this many values per thread (measured: faster with 16, slower
+// with 8, where fewer independent chains are in flight).
+#ifndef HFS_PACK_PHASE_MIN_E
+#define HFS_PACK_PHASE_MIN_E 16
+#endif
 template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
 {
 #ifndef HFS_NO_PHASE_FENCE
@@ -64,22 +73,34 @@ template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E]
 }
 
 // merged x-phase X_j on the register layout (position t + T e)
+// the phase argument of one point (turns) before the B-flow term
+__device__ __forceinline__ float xphase_F(cpx<float> u, float mf, const TeamParams<float> &tp)
+{
+    const float x = fmaf(mf, tp.dx, tp.xc);
+    const float dens = u.x * u.x + u.y * u.y;
+    return fmaf(tp.sigma, dens, tp.eps * vi_eval(tp.vikind, x, tp.vik));
+}
+
 template <int N, int E>
 __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp)
 {
     constexpr int T = N / E;
+    constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
+    static_assert(E % 2 == 0 && PHASE_GROUP % 2 == 0, "points are phased in pairs");
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E; e += 2) {
         if (e % PHASE_GROUP == 0) fence_group(v, e);
-        const int m = t + T * e - N / 2;
-        const float mf = (float)m;
-        float turns = frac_turns((float)(m * m), rc.k2hi, rc.k2lo);
-        if (tp.asym) turns += frac_turns(mf, rc.k1hi, rc.k1lo) + rc.k0;
-        const float x = fmaf(mf, tp.dx, tp.xc);
-        const float dens = v[e].x * v[e].x + v[e].y * v[e].y;
-        const float F = fmaf(tp.sigma, dens, tp.eps * vi_eval(tp.vikind, x, tp.vik));
-        turns = fmaf(rc.sb2pi, F, turns);
-        v[e] = apply_turns(v[e], turns, 1.0f);
+        const int m0 = t + T * e - N / 2, m1 = m0 + T;
+        const float2 mf = make_float2((float)m0, (float)m1);
+        float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.k2hi, rc.k2lo);
+        if (tp.asym) {
+            const float2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
+            turns = make_float2(turns.x + (lin.x + rc.k0), turns.y + (lin.y + rc.k0));
+        }
+        const float2 F = make_float2(xphase_F(v[e], mf.x, tp), xphase_F(v[e + 1], mf.y, tp));
+        if constexpr (PK) turns = __ffma2_rn(bc2(rc.sb2pi), F, turns);
+        else turns = make_float2(fmaf(rc.sb2pi, F.x, turns.x), fmaf(rc.sb2pi, F.y, turns.y));
+        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f);
     }
 }
 
@@ -105,13 +126,15 @@ __device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &r
 template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E], int t, const RecF &rc)
 {
     constexpr int T = N / E;
+    constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E; e += 2) {
         if (e % PHASE_GROUP == 0) fence_group(v, e);
-        const int k = t + T * e;
-        const int m = (k < N / 2) ? k : k - N;
-        const float turns = frac_turns((float)(m * m), rc.ghi, rc.glo);
-        v[e] = apply_turns(v[e], turns, 1.0f / N);
+        const int k0 = t + T * e, k1 = k0 + T;
+        const int m0 = (k0 < N / 2) ? k0 : k0 - N;
+        const int m1 = (k1 < N / 2) ? k1 : k1 - N;
+        const float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.ghi, rc.glo);
+        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f / N);
     }
 }
 
