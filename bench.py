@@ -46,9 +46,9 @@ COUNT, STEPS, DT = 4096, 500, 0.005
 # DRAM bytes per launch of the fused step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same command, summarised in
 # profiles/), valid only while the kernel's sources hash to "src".
-STEP1D_TRAFFIC = {"src": "58b5a2b8aee2290a",
-                  "batch_1d_4096x500_c64": 111118592 + 627253248,
-                  "batch_1d_65536x1_streaming": (731394816 + 1070601984 + 731420672 + 1064741888) // 2}
+STEP1D_TRAFFIC = {"src": "8b9de0f80dcfb1ac",
+                  "batch_1d_4096x500_c64": 110682112 + 45686272,
+                  "batch_1d_65536x1_streaming": (731320064 + 826665216 + 730971392 + 822957312) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cu", "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_law.cuh", "hfs_sched.h")
 
 
