@@ -193,8 +193,8 @@ template <int RAD, bool INV, typename R> __device__ __forceinline__ void dft_any
     else static_assert(RAD == 2, "unsupported radix");
 }
 
-// Twiddle tables exp(-2 pi i k/n): FP32 entries are (hi.re, hi.im, lo.re,
-// lo.im) with hi + lo the FP64 value; FP64 entries are plain.
+// Twiddle tables (layout: tw_pass_offset): FP32 entries are (hi.re, hi.im,
+// lo.re, lo.im) with hi + lo the FP64 value; FP64 entries are plain.
 template <typename R> struct TwOf;
 template <> struct TwOf<float> { using type = float4; };
 template <> struct TwOf<double> { using type = double2; };
@@ -262,10 +262,11 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
         for (int r = 0; r < RAD; ++r) a[r] = v[q + r * Q];
         const int j = b & (NS - 1);
         if constexpr (NS > 1) {
-            constexpr int STRIDE = N / (NS * RAD);
-            const int js = j * STRIDE;
+            // W_{NS RAD}^{j r} from this pass shape's region of the table
+            constexpr int64_t OFF = tw_pass_offset(NS * RAD, RAD);
+            static_assert(NS * RAD <= kTwiddleMaxLength, "twiddle table too short");
 #pragma unroll
-            for (int r = 1; r < RAD; ++r) a[r] = tw_mul<INV>(a[r], twp, js * r);
+            for (int r = 1; r < RAD; ++r) a[r] = tw_mul<INV>(a[r], twp, (int)(OFF + (r - 1) * NS) + j);
         }
         dft_any<RAD, INV>(a);
         if constexpr (LAST) {

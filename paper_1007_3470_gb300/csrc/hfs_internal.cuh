@@ -121,9 +121,24 @@ __host__ __device__ constexpr int plan_id(int n, int ept) { return size_class(n)
 
 constexpr int kCtaThreads = 256;
 
-// twiddle table: concatenation of exp(-2 pi i k / n), k < n, for n = 16..4096
-// (powers of two); the table of size n starts at 16 + 32 + ... + n/2 = n - 16
-__host__ __device__ constexpr int64_t twiddle_offset(int n) { return n - 16; }
-constexpr int64_t kTwiddleTotal = 8192 - 16;
+// Twiddle table, one region per Stockham pass shape: a radix-R pass that
+// forms sub-transforms of length L = NS R (NS >= 2 earlier length) needs
+// exp(-2 pi i j r / L) for r = 1..R-1, j = 0..NS-1, stored at
+// tw_pass_offset(L, R) + (r - 1) NS + j, so the lanes of a warp (consecutive
+// j) read consecutive entries.  Regions for L = 4..4096, R = 2, 4, 8, 16.
+__host__ __device__ constexpr int64_t tw_region_size(int L, int R) { return (R <= L / 2) ? (int64_t)(L / R) * (R - 1) : 0; }
+__host__ __device__ constexpr int64_t tw_length_size(int L)
+{
+    return tw_region_size(L, 2) + tw_region_size(L, 4) + tw_region_size(L, 8) + tw_region_size(L, 16);
+}
+__host__ __device__ constexpr int64_t tw_pass_offset(int L, int R)
+{
+    int64_t off = 0;
+    for (int l = 4; l < L; l <<= 1) off += tw_length_size(l);
+    for (int r = 2; r < R; r <<= 1) off += tw_region_size(L, r);
+    return off;
+}
+constexpr int kTwiddleMaxLength = 4096;
+constexpr int64_t kTwiddleTotal = tw_pass_offset(2 * kTwiddleMaxLength, 2);
 
 }  // namespace hfs

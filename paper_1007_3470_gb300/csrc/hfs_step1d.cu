@@ -163,7 +163,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     const TeamParams<R> tp = team_params<R>(ip);
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + ip.off;
     cpx<R> *sm = smem + g * smem_elems(N);
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     const Rec *rec = reinterpret_cast<const Rec *>(a.rec) + (int64_t)idx * a.nrec;
 
     cpx<R> v[E];
@@ -254,7 +254,7 @@ __device__ __forceinline__ void diag_item(const Diag1DArgs &a, const WorkItem &i
     const DevInst &ip = a.inst[idx];
     const cpx<R> *psi = reinterpret_cast<const cpx<R> *>(a.psi) + ip.off;
     cpx<R> *sm = smem + g * smem_elems(N);
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     const double w2 = law_omega2(ip, *a.t_dev);
     cpx<R> v[E];
     double nrm = 0.0, pot = 0.0, inter = 0.0, kin = 0.0;
@@ -319,20 +319,24 @@ template <typename R> __global__ void __launch_bounds__(kCtaThreads) diag1d_kern
 }
 
 // ---------------------------------------------------------------------------
-// twiddle tables exp(-2 pi i k / n) for n = 16..4096, computed in FP64
-// ---------------------------------------------------------------------------
+// twiddle tables (layout: tw_pass_offset), computed in FP64: entry
+// (r - 1) NS + j of region (L, R) is exp(-2 pi i j r / L)
 __global__ void twiddle_kernel(float4 *tf, double2 *td)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= kTwiddleTotal) return;
-    int n = 16;
-    while (i >= twiddle_offset(n) + n) n <<= 1;
-    const int64_t k = i - twiddle_offset(n);
-    double s, c;
-    sincospi(2.0 * (double)k / (double)n, &s, &c);
-    td[i] = make_double2(c, -s);
-    const float ch = (float)c, sh = (float)-s;
-    tf[i] = make_float4(ch, sh, (float)(c - (double)ch), (float)(-s - (double)sh));
+    int L = 4;
+    while (i >= tw_pass_offset(2 * L, 2)) L <<= 1;
+    int R = 2;
+    while (R < 16 && i >= tw_pass_offset(L, 2 * R)) R <<= 1;
+    const int64_t s = i - tw_pass_offset(L, R);
+    const int NS = L / R;
+    const int64_t r = s / NS + 1, j = s % NS;
+    double sn, cs;
+    sincospi(2.0 * (double)(j * r) / (double)L, &sn, &cs);
+    td[i] = make_double2(cs, -sn);
+    const float ch = (float)cs, sh = (float)-sn;
+    tf[i] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(-sn - (double)sh));
 }
 
 // ---------------------------------------------------------------------------

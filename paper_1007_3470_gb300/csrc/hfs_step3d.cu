@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kCtaThreads) xpass3d(const Step3DArgs a, int64
     const int y = line % N, z = line / N;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + g * smem_elems(N);
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)line * N;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[t + T * e];
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kCtaThreads) ypass3d(const Step3DArgs a)
     const int z = blockIdx.y, x0 = blockIdx.x * TX;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)z * N * N + x0 + l;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N];
@@ -125,7 +125,7 @@ template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpas
     const int y = blockIdx.y, x = blockIdx.x * TX + l;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)y * N + x;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
@@ -165,7 +165,7 @@ template <int MODE> __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(
     cpx<float> *pl = reinterpret_cast<cpx<float> *>(smem_raw);
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
-    const auto *tw = reinterpret_cast<const float4 *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const float4 *>(a.tw);
     // load the plane: element (y, x) -> row y, padded slot of x
     for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) pl[(i / N) * kPlaneRow + spad(i % N)] = psi[i];
     __syncthreads();
@@ -275,7 +275,7 @@ template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) diag
     const int y = line % N, z = line / N;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + g * smem_elems(N);
     const cpx<R> *psi = reinterpret_cast<const cpx<R> *>(a.psi) + (int64_t)line * N;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     const DevInst &ip = *a.inst;
     const double w2 = law_omega2(ip, *a.t_dev);
     const double dx = ip.dx[0];
@@ -320,7 +320,7 @@ template <typename R, int N, int AXIS> __global__ void __launch_bounds__(kCtaThr
     const int64_t base = (AXIS == 1) ? (int64_t)other * N * N + x : (int64_t)other * N + x;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
     const cpx<R> *psi = reinterpret_cast<const cpx<R> *>(a.psi) + base;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw) + twiddle_offset(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     const DevInst &ip = *a.inst;
     cpx<R> v[E];
 #pragma unroll
