@@ -46,9 +46,9 @@ COUNT, STEPS, DT = 4096, 500, 0.005
 # DRAM bytes per launch of the fused step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same command, summarised in
 # profiles/), valid only while the kernel's sources hash to "src".
-STEP1D_TRAFFIC = {"src": "8b9de0f80dcfb1ac",
-                  "batch_1d_4096x500_c64": 110682112 + 45686272,
-                  "batch_1d_65536x1_streaming": (731320064 + 826665216 + 730971392 + 822957312) // 2}
+STEP1D_TRAFFIC = {"src": "e87bb6820241d7a9",
+                  "batch_1d_4096x500_c64": 110389760 + 44314880,
+                  "batch_1d_65536x1_streaming": (730957056 + 847138048 + 730955520 + 843006976) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cu", "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_law.cuh", "hfs_sched.h")
 
 
@@ -494,7 +494,7 @@ def run_reference(args):
     O.build()
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; each step below is a full bounded sample
-    insts, psis = _stratified_sample(args.cpu_sample, 20100703)
+    insts, psis = _stratified_sample(args.ref_sample, 20100703)
     probs = [O.Problem(**i.as_dict()) for i in insts]
     cores = O.max_threads()
     gps = sum(i.n[0] for i in insts) * STEPS
@@ -505,7 +505,6 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = gps * args.steps / total
-    workload = f"batch_1d_{COUNT_}x{STEPS_}_c64"
     line = {
         "metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -514,7 +513,7 @@ def run_reference(args):
                    "sample_per_step": f"{len(insts)} instances stratified over grid sizes"},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{len(insts)} instances ({args.cpu_sample} per grid size) x {STEPS} steps per step"},
+                         "sample": f"{len(insts)} instances ({args.ref_sample} per grid size) x {STEPS} steps per step"},
         "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -526,7 +525,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--cpu-sample", type=int, default=16, help="instances per grid size in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=320,
+                    help="instances per grid size in the cpu_baseline oracle sample (about 15 s on 16 cores)")
+    ap.add_argument("--ref-sample", type=int, default=48,
+                    help="instances per grid size in each step of --impl reference (about 2 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

@@ -114,13 +114,13 @@ __device__ __forceinline__ void dft4p(cpx<float> &a0, cpx<float> &a1, cpx<float>
     a1 = cadd_rot_p<INV ? -1 : 1>(t1, d);
     a3 = cadd_rot_p<INV ? 1 : -1>(t1, d);
 }
-// Radix-4 stage of the radix-16 and radix-8 butterflies: packed in FP32
-// where that measured faster (radix 16).
+// Radix-4 stages of the radix-16 and radix-8 butterflies in packed FP32
+// (both measured faster than the scalar form).
 #ifndef HFS_PACK_DFT16
 #define HFS_PACK_DFT16 1
 #endif
 #ifndef HFS_PACK_DFT8
-#define HFS_PACK_DFT8 0
+#define HFS_PACK_DFT8 1
 #endif
 template <bool INV, bool PACK, typename R>
 __device__ __forceinline__ void dft4s(cpx<R> &a0, cpx<R> &a1, cpx<R> &a2, cpx<R> &a3)

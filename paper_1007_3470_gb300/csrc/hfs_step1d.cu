@@ -54,10 +54,10 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
 #endif
 constexpr int PHASE_GROUP = HFS_PHASE_GROUP;
 // Phase arithmetic of point pairs in packed FP32 instructions for plans with
-// at least this many values per thread (measured: faster with 16, slower
-// with 8, where fewer independent chains are in flight).
+// at least this many values per thread (all plans; measured 2-5 % faster
+// than the scalar form for both 8 and 16 values per thread).
 #ifndef HFS_PACK_PHASE_MIN_E
-#define HFS_PACK_PHASE_MIN_E 16
+#define HFS_PACK_PHASE_MIN_E 8
 #endif
 template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
 {
