@@ -32,4 +32,47 @@ __device__ __forceinline__ double axis_omega2(const DevInst &p, int dim, int axi
     return c * c * law_omega2(p, t);
 }
 
+// sin and cos of a small angle (|d| <= 1/32) by their Taylor series (the
+// first omitted terms are below 1e-21), otherwise by sincos
+__device__ __forceinline__ void sincos_small(double d, double &s, double &c)
+{
+    if (fabs(d) <= 0.03125) {
+        const double d2 = d * d;
+        s = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
+        c = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0))));
+    } else {
+        sincos(d, &s, &c);
+    }
+}
+
+// omega^2 at the two symmetric nodes tm - d and tm + d (the Gauss nodes of a
+// stage): the periodic laws take both from one sincos of the midpoint
+// argument, sin(th -+ de) = sin th cos de -+ cos th sin de
+__device__ __forceinline__ void axis_omega2_pair(const DevInst &p, int dim, int axis, double tm, double d,
+                                                 double &w1, double &w2)
+{
+    const double c = (dim == 1) ? 1.0 : p.axis_scale[axis];
+    const double c2 = c * c;
+    if (p.omega_law == HFS_OMEGA_SIN) {
+        double st, ct, sd, cd;
+        sincos(fma(p.law[1], tm, p.law[2]), &st, &ct);
+        sincos_small(p.law[1] * d, sd, cd);
+        const double a = st * cd, b = ct * sd;
+        const double u1 = p.w0 * (1.0 + p.law[0] * (a - b)), u2 = p.w0 * (1.0 + p.law[0] * (a + b));
+        w1 = c2 * (u1 * u1);
+        w2 = c2 * (u2 * u2);
+    } else if (p.omega_law == HFS_OMEGA_COS_SQ) {
+        double st, ct, sd, cd;
+        sincos(p.law[1] * tm, &st, &ct);
+        sincos_small(p.law[1] * d, sd, cd);
+        const double a = ct * cd, b = st * sd;
+        const double k = p.w0 * p.w0;
+        w1 = c2 * (k * (1.0 + p.law[0] * (a + b)));
+        w2 = c2 * (k * (1.0 + p.law[0] * (a - b)));
+    } else {
+        w1 = axis_omega2(p, dim, axis, tm - d);
+        w2 = axis_omega2(p, dim, axis, tm + d);
+    }
+}
+
 }  // namespace hfs

@@ -92,8 +92,9 @@ __device__ void fge_thm2(double wl, double wr, double s, double &f, double &g, d
     g = L.S * Rr.C + L.C * Rr.S;
     const double omcc = L.OMC + L.C * Rr.OMC;  // 1 - C_L C_R
     const double ss = L.S * Rr.S;
-    f = (omcc + wl * ss) / g;
-    e = (omcc + wr * ss) / g;
+    const double ig = 1.0 / g;
+    f = (omcc + wl * ss) * ig;
+    e = (omcc + wr * ss) * ig;
 }
 
 // Theorem 1 for exp(-i s/2 (al x^2 + be (xp+px) + ga p^2))
@@ -101,8 +102,9 @@ __device__ void fge_thm1(double al, double be, double ga, double s, double &f, d
 {
     const CS r = cs_of(al * ga - be * be, s);
     g = ga * r.S;
-    f = (r.OMC + be * r.S) / g;
-    e = (r.OMC - be * r.S) / g;
+    const double ig = 1.0 / g;
+    f = (r.OMC + be * r.S) * ig;
+    e = (r.OMC - be * r.S) * ig;
 }
 
 __device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double tau, double s, double &f,
@@ -119,14 +121,14 @@ __device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double 
         const double r3 = 0.28867513459481288225;  // sqrt(3)/6
         const double al = 0.5 - 2.0 * r3;          // 1/2 - 1/sqrt(3)
         const double be = 1.0 - al;
-        const double w1 = axis_omega2(p, dim, axis, tau + (0.5 - r3) * s);
-        const double w2 = axis_omega2(p, dim, axis, tau + (0.5 + r3) * s);
+        double w1, w2;
+        axis_omega2_pair(p, dim, axis, tau + 0.5 * s, r3 * s, w1, w2);
         fge_thm2(al * w1 + be * w2, be * w1 + al * w2, s, f, g, e);
     } else {
         const double r15 = 0.38729833462074168852;  // sqrt(15)/10
-        const double w1 = axis_omega2(p, dim, axis, tau + (0.5 - r15) * s);
+        double w1, w3;
+        axis_omega2_pair(p, dim, axis, tau + 0.5 * s, r15 * s, w1, w3);
         const double w2 = axis_omega2(p, dim, axis, tau + 0.5 * s);
-        const double w3 = axis_omega2(p, dim, axis, tau + (0.5 + r15) * s);
         const double s2 = s * s;
         const double avg = 5.0 * w1 + 8.0 * w2 + 5.0 * w3;
         const double al = avg / 18.0 + s2 / 486.0 * (4.25 * (w1 * w1 + w3 * w3) + 8.0 * w2 * w2 + w1 * w2 +
@@ -136,9 +138,11 @@ __device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double 
         fge_thm1(al, be, ga, s, f, g, e);
     }
     // mass: the mu-problem is the mu = 1 problem conjugated by diag(1, mu)
-    f *= p.mu;
-    e *= p.mu;
-    g /= p.mu;
+    if (p.mu != 1.0) {
+        f *= p.mu;
+        e *= p.mu;
+        g /= p.mu;
+    }
 }
 
 // one thread per (instance, stage in chunk)

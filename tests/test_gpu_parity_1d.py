@@ -71,6 +71,26 @@ def test_schedule_variants(precision, tol, comp, flow, split):
     assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
 
 
+@pytest.mark.parametrize("law,lawp", [(W.OMEGA_COS_SQ, [0.3, 2.0, 0.0]),   # small node offset: series path
+                                      (W.OMEGA_COS_SQ, [0.3, 40.0, 0.0]),  # law[1] s r3 > 1/32: sincos path
+                                      (W.OMEGA_SIN, [0.4, 30.0, 0.7]),
+                                      (W.OMEGA_PULSE, [0.5, 2.0, 1.0])])
+@pytest.mark.parametrize("flow", [1, 2])  # Magnus-4 + Theorem 2, Magnus-6 + Theorem 1
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_trap_laws_and_magnus_flows(precision, tol, law, lawp, flow):
+    """Every time-dependent trap law of Sec. 4.2 under both Magnus flows,
+    including fast laws whose Gauss-node offsets leave the small-angle range."""
+    need_gpu()
+    inst = W.Instance(n=[512], a=[-14.0], b=[14.0], omega_law=law, w0=1.1, law=lawp, eps=0.05,
+                      vi_kind=W.VI_COS, vi_k=1.5, sigma=5.0, ho_flow=flow, h=0.01)
+    x = inst.x()
+    psi0 = (1.1 / math.pi) ** 0.25 * np.exp(-1.1 * (x - 0.5) ** 2 / 2).astype(complex)
+    steps = 200
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    (out,) = _run_gpu([inst], [psi0], steps, precision, inst.h, flow=flow)
+    assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+
+
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_asymmetric_box_and_mass(precision, tol):
     """A box not centred at 0 (K1, K0 terms of the chirp) and mu != 1."""
