@@ -96,6 +96,8 @@ struct hfs_ctx_s {
     int64_t elems = 0;
     // 1D plans: elements per thread per size class
     int ept[kNumSizes] = {16, 16, 16, 16, 16, 16};
+    // trap law shared by every instance (HFS_OMEGA_*), -1 for a mixed batch
+    int law = -1;
     std::vector<int32_t> order;  // sorted position -> instance
     std::vector<WorkItem> work;
     // schedule
@@ -265,7 +267,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
         const int64_t nstage = S * m;
         const double toff = (double)done * c->sc.h;
         if (c->sc.split == HFS_SPLIT_HO)
-            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, fge, status, c->stream));
+            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, c->law, fge, status, c->stream));
         if (c->dim == 1) {
             CK(launch_records1d(fp64, dinst, c->count, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
             Step1DArgs a{};
@@ -353,6 +355,7 @@ int hfs_create(hfs_ctx_t *out, int dim, int precision, const hfs_instance *inst,
     c->precision = precision;
     c->count = count;
     c->inst.assign(inst, inst + count);
+    c->law = uniform_law(inst, count);
     c->dinst.resize(count);
     c->offsets.resize(count);
     int64_t off = 0;

@@ -5,10 +5,12 @@
 
 namespace hfs {
 
-__device__ __forceinline__ double law_omega2(const DevInst &p, double t)
+// LAW >= 0: the law is known at compile time (every instance of a batch uses
+// it); LAW = -1 reads it from the instance
+template <int LAW = -1> __device__ __forceinline__ double law_omega2(const DevInst &p, double t)
 {
     double w;
-    switch (p.omega_law) {
+    switch (LAW >= 0 ? LAW : p.omega_law) {
     case HFS_OMEGA_CONST:
         return p.w0 * p.w0;
     case HFS_OMEGA_SIN:
@@ -26,10 +28,10 @@ __device__ __forceinline__ double law_omega2(const DevInst &p, double t)
     }
 }
 
-__device__ __forceinline__ double axis_omega2(const DevInst &p, int dim, int axis, double t)
+template <int LAW = -1> __device__ __forceinline__ double axis_omega2(const DevInst &p, int dim, int axis, double t)
 {
     const double c = (dim == 1) ? 1.0 : p.axis_scale[axis];
-    return c * c * law_omega2(p, t);
+    return c * c * law_omega2<LAW>(p, t);
 }
 
 // sin and cos of a small angle (|d| <= 1/32) by their Taylor series (the
@@ -48,12 +50,14 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c)
 // omega^2 at the two symmetric nodes tm - d and tm + d (the Gauss nodes of a
 // stage): the periodic laws take both from one sincos of the midpoint
 // argument, sin(th -+ de) = sin th cos de -+ cos th sin de
+template <int LAW = -1>
 __device__ __forceinline__ void axis_omega2_pair(const DevInst &p, int dim, int axis, double tm, double d,
                                                  double &w1, double &w2)
 {
     const double c = (dim == 1) ? 1.0 : p.axis_scale[axis];
     const double c2 = c * c;
-    if (p.omega_law == HFS_OMEGA_SIN) {
+    const int law = LAW >= 0 ? LAW : p.omega_law;
+    if (law == HFS_OMEGA_SIN) {
         double st, ct, sd, cd;
         sincos(fma(p.law[1], tm, p.law[2]), &st, &ct);
         sincos_small(p.law[1] * d, sd, cd);
@@ -61,7 +65,7 @@ __device__ __forceinline__ void axis_omega2_pair(const DevInst &p, int dim, int 
         const double u1 = p.w0 * (1.0 + p.law[0] * (a - b)), u2 = p.w0 * (1.0 + p.law[0] * (a + b));
         w1 = c2 * (u1 * u1);
         w2 = c2 * (u2 * u2);
-    } else if (p.omega_law == HFS_OMEGA_COS_SQ) {
+    } else if (law == HFS_OMEGA_COS_SQ) {
         double st, ct, sd, cd;
         sincos(p.law[1] * tm, &st, &ct);
         sincos_small(p.law[1] * d, sd, cd);
@@ -70,8 +74,8 @@ __device__ __forceinline__ void axis_omega2_pair(const DevInst &p, int dim, int 
         w1 = c2 * (k * (1.0 + p.law[0] * (a + b)));
         w2 = c2 * (k * (1.0 + p.law[0] * (a - b)));
     } else {
-        w1 = axis_omega2(p, dim, axis, tm - d);
-        w2 = axis_omega2(p, dim, axis, tm + d);
+        w1 = axis_omega2<LAW>(p, dim, axis, tm - d);
+        w2 = axis_omega2<LAW>(p, dim, axis, tm + d);
     }
 }
 

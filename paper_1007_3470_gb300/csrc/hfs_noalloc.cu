@@ -190,7 +190,7 @@ extern "C" int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *
         const int64_t nstage = S * sc.m;
         const double toff = (double)done * dt;
         if (split == HFS_SPLIT_HO)
-            HFS_NA_CK(launch_stage_flow(dinst, count, 1, sc, tdev, toff, nstage, fge, status, st));
+            HFS_NA_CK(launch_stage_flow(dinst, count, 1, sc, tdev, toff, nstage, uniform_law(inst, count), fge, status, st));
         HFS_NA_CK(launch_records1d(fp64, dinst, count, sc, tdev, toff, nstage, fge, rec, status, st));
         Step1DArgs a{};
         a.psi = psi;

@@ -30,6 +30,9 @@
 // time.
 #include <math.h>
 
+#include <algorithm>
+#include <cstdint>
+
 #include "hfs_internal.cuh"
 #include "hfs_law.cuh"
 #include "hfs_sched.h"
@@ -44,6 +47,16 @@ __device__ CS cs_of(double w, double t)
 {
     CS r;
     const double z = w * t * t;  // theta^2, negative for w < 0
+    if (fabs(z) <= 1e-3) {
+        // the same series to z^3: the first omitted terms, z^4/10! and z^4/9!,
+        // are below 3e-18 of the sums
+        const double c = fma(fma(fma(-z, 1.0 / 40320.0, 1.0 / 720.0), -z, 1.0 / 24.0), -z, 0.5);
+        const double sv = fma(fma(fma(-z, 1.0 / 5040.0, 1.0 / 120.0), -z, 1.0 / 6.0), -z, 1.0);
+        r.OMC = z * c;
+        r.C = 1.0 - r.OMC;
+        r.S = t * sv;
+        return r;
+    }
     if (fabs(z) <= 0.25) {
         // Power series of the entire functions in z = w t^2 (Taylor series of
         // cos and sin / theta), eight terms: truncation below 1e-18.  No square
@@ -107,28 +120,31 @@ __device__ void fge_thm1(double al, double be, double ga, double s, double &f, d
     e = (r.OMC - be * r.S) * ig;
 }
 
-__device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double tau, double s, double &f,
-                          double &g, double &e)
+// FLOW (and, when a batch shares one trap law, LAW) are template parameters:
+// with a run-time flow the compiler evaluated all three branches and kept one
+// result (3.6x the FP64 work)
+template <int FLOW, int LAW>
+__device__ void stage_fge(const DevInst &p, int dim, int axis, double tau, double s, double &f, double &g, double &e)
 {
-    if (flow == HFS_FLOW_LEMMA2) {
-        const double om = sqrt(axis_omega2(p, dim, axis, tau));
+    if constexpr (FLOW == HFS_FLOW_LEMMA2) {
+        const double om = sqrt(axis_omega2<LAW>(p, dim, axis, tau));
         double sh, ch;
         sincos(0.5 * om * s, &sh, &ch);
         g = 2.0 * sh * ch / om;
         f = om * sh / ch;
         e = f;
-    } else if (flow == HFS_FLOW_CF4) {
+    } else if constexpr (FLOW == HFS_FLOW_CF4) {
         const double r3 = 0.28867513459481288225;  // sqrt(3)/6
         const double al = 0.5 - 2.0 * r3;          // 1/2 - 1/sqrt(3)
         const double be = 1.0 - al;
         double w1, w2;
-        axis_omega2_pair(p, dim, axis, tau + 0.5 * s, r3 * s, w1, w2);
+        axis_omega2_pair<LAW>(p, dim, axis, tau + 0.5 * s, r3 * s, w1, w2);
         fge_thm2(al * w1 + be * w2, be * w1 + al * w2, s, f, g, e);
     } else {
         const double r15 = 0.38729833462074168852;  // sqrt(15)/10
         double w1, w3;
-        axis_omega2_pair(p, dim, axis, tau + 0.5 * s, r15 * s, w1, w3);
-        const double w2 = axis_omega2(p, dim, axis, tau + 0.5 * s);
+        axis_omega2_pair<LAW>(p, dim, axis, tau + 0.5 * s, r15 * s, w1, w3);
+        const double w2 = axis_omega2<LAW>(p, dim, axis, tau + 0.5 * s);
         const double s2 = s * s;
         const double avg = 5.0 * w1 + 8.0 * w2 + 5.0 * w3;
         const double al = avg / 18.0 + s2 / 486.0 * (4.25 * (w1 * w1 + w3 * w3) + 8.0 * w2 * w2 + w1 * w2 +
@@ -145,44 +161,48 @@ __device__ void stage_fge(const DevInst &p, int dim, int axis, int flow, double 
     }
 }
 
-// one thread per (instance, stage in chunk)
-__global__ void stage_flow_kernel(const DevInst *__restrict__ inst, int64_t count, int dim, SchedConst sc,
-                                  const double *__restrict__ t_dev, double t_off, int64_t nstage,
-                                  StageFGE *__restrict__ out, unsigned *status)
+// one thread per (instance, time step of the chunk), all m stages of the
+// step: instance = blockIdx.x, steps strided over blockIdx.y / threadIdx.x
+// (no 64-bit integer division in the index arithmetic)
+template <int FLOW, int LAW>
+__global__ void stage_flow_kernel(const DevInst *__restrict__ inst, int dim, SchedConst sc,
+                                  const double *__restrict__ t_dev, double t_off, int nsteps, StageFGE *__restrict__ out,
+                                  unsigned *status)
 {
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= count * nstage) return;
-    const int64_t i = gid / nstage;
-    const int64_t sg = gid - i * nstage;
-    const int64_t n = sg / sc.m;
-    const int st = (int)(sg - n * sc.m);
-    const double t0 = *t_dev + t_off;
-    const double tau = t0 + (double)n * sc.h + sc.h * sc.cuma[st];
-    const double s = sc.a[st] * sc.h;
+    const int64_t i = blockIdx.x;
     const DevInst p = inst[i];
-    for (int d = 0; d < dim; ++d) {
-        double f, g, e;
-        stage_fge(p, dim, d, sc.flow, tau, s, f, g, e);
-        if (!isfinite(f) || !isfinite(g) || !isfinite(e)) atomicOr(status, (unsigned)ST_NONFINITE);
-        StageFGE r;
-        r.f = f;
-        r.g = g;
-        r.e = e;
-        r.tau = tau;
-        out[(i * nstage + sg) * dim + d] = r;
+    const double t0 = *t_dev + t_off;
+    const int64_t nstage = (int64_t)nsteps * sc.m;
+    for (int n = blockIdx.y * blockDim.x + threadIdx.x; n < nsteps; n += gridDim.y * blockDim.x) {
+        for (int st = 0; st < sc.m; ++st) {
+            const double tau = t0 + (double)n * sc.h + sc.h * sc.cuma[st];
+            const double s = sc.a[st] * sc.h;
+            const int64_t sg = (int64_t)n * sc.m + st;
+            for (int d = 0; d < dim; ++d) {
+                double f, g, e;
+                stage_fge<FLOW, LAW>(p, dim, d, tau, s, f, g, e);
+                if (!isfinite(f) || !isfinite(g) || !isfinite(e)) atomicOr(status, (unsigned)ST_NONFINITE);
+                StageFGE r;
+                r.f = f;
+                r.g = g;
+                r.e = e;
+                r.tau = tau;
+                out[(i * nstage + sg) * dim + d] = r;
+            }
+        }
     }
 }
 
 // kick coefficient kappa, B sum and drift g of sub-stage j on axis d
-__device__ void merged_coeffs(const DevInst &p, int dim, int d, const SchedConst &sc, double t0, int64_t j,
-                              int64_t nstage, const StageFGE *__restrict__ fge_i, double &kappa, double &bs,
-                              double &g)
+template <int SPLIT>
+__device__ void merged_coeffs(const DevInst &p, int dim, int d, const SchedConst &sc, double t0, int j, int nstage,
+                              const StageFGE *__restrict__ fge_i, double &kappa, double &bs, double &g)
 {
-    const int64_t mm = sc.m;
-    const int64_t r = j % mm;
+    const int mm = sc.m;
+    const int r = j % mm;
     if (r == 0) bs = (j > 0 ? sc.b[mm] : 0.0) + (j < nstage ? sc.b[0] : 0.0);
     else bs = sc.b[r];
-    if (sc.split == HFS_SPLIT_HO) {
+    if constexpr (SPLIT == HFS_SPLIT_HO) {
         kappa = 0.0;
         if (j >= 1) kappa += fge_i[(j - 1) * dim + d].f;
         if (j < nstage) kappa += fge_i[j * dim + d].e;
@@ -207,21 +227,13 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
 
-// one thread per (instance, sub-stage j in [0, nstage]) -- 1D records
-template <typename RecT>
-__global__ void records1d_kernel(const DevInst *__restrict__ inst, int64_t count, SchedConst sc,
-                                 const double *__restrict__ t_dev, double t_off, int64_t nstage,
-                                 const StageFGE *__restrict__ fge, RecT *__restrict__ rec, unsigned *status)
+// the phase record of 1D sub-stage j (turns per integer index, see above)
+template <typename RecT, int SPLIT>
+__device__ __forceinline__ void record1d(const DevInst &p, const SchedConst &sc, double t0, int j, int nstage,
+                                         const StageFGE *__restrict__ fge_i, RecT *out, unsigned *status)
 {
-    const int64_t nrec = nstage + 1;
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= count * nrec) return;
-    const int64_t i = gid / nrec;
-    const int64_t j = gid - i * nrec;
-    const DevInst p = inst[i];
-    const double t0 = *t_dev + t_off;
     double kappa, bs, g;
-    merged_coeffs(p, 1, 0, sc, t0, j, nstage, fge + i * nstage, kappa, bs, g);
+    merged_coeffs<SPLIT>(p, 1, 0, sc, t0, j, nstage, fge_i, kappa, bs, g);
     const double K2 = kappa * p.dx[0] * p.dx[0] * kInv4Pi;
     const double K1 = kappa * p.xc[0] * p.dx[0] * kInv2Pi;
     const double K0 = frac1(kappa * p.xc[0] * p.xc[0] * kInv4Pi);
@@ -243,16 +255,31 @@ __global__ void records1d_kernel(const DevInst *__restrict__ inst, int64_t count
         r.g = G;
         r.pad = 0.0;
     }
-    rec[gid] = r;
+    *out = r;
+}
+
+// one thread per (instance, sub-stage j in [0, nstage]) -- 1D records;
+// instance = blockIdx.x, sub-stages strided over blockIdx.y / threadIdx.x
+template <typename RecT, int SPLIT>
+__global__ void records1d_kernel(const DevInst *__restrict__ inst, SchedConst sc, const double *__restrict__ t_dev,
+                                 double t_off, int nstage, const StageFGE *__restrict__ fge, RecT *__restrict__ rec,
+                                 unsigned *status)
+{
+    const int64_t i = blockIdx.x;
+    const int64_t nrec = (int64_t)nstage + 1;
+    const DevInst p = inst[i];
+    const double t0 = *t_dev + t_off;
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j <= nstage; j += gridDim.y * blockDim.x)
+        record1d<RecT, SPLIT>(p, sc, t0, j, nstage, fge + i * (int64_t)nstage, rec + i * nrec + j, status);
 }
 
 // 3D records (symmetric boxes): one per sub-stage, all three axes
-template <typename RecT>
+template <typename RecT, int SPLIT>
 __global__ void records3d_kernel(const DevInst *__restrict__ inst, SchedConst sc, const double *__restrict__ t_dev,
-                                 double t_off, int64_t nstage, const StageFGE *__restrict__ fge,
+                                 double t_off, int nstage, const StageFGE *__restrict__ fge,
                                  RecT *__restrict__ rec, unsigned *status)
 {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > nstage) return;
     const DevInst p = inst[0];
     const double t0 = *t_dev + t_off;
@@ -260,7 +287,7 @@ __global__ void records3d_kernel(const DevInst *__restrict__ inst, SchedConst sc
     double SB = 0.0;
     for (int d = 0; d < 3; ++d) {
         double kappa, bs, g;
-        merged_coeffs(p, 3, d, sc, t0, j, nstage, fge, kappa, bs, g);
+        merged_coeffs<SPLIT>(p, 3, d, sc, t0, j, nstage, fge, kappa, bs, g);
         const double K2 = kappa * p.dx[d] * p.dx[d] / (4.0 * kPi);
         const double G = g * kPi / (p.len[d] * p.len[d]);
         SB = bs * sc.h / (2.0 * kPi);
@@ -287,12 +314,49 @@ __global__ void advance_time_kernel(double *t_dev, double dt) { *t_dev += dt; }
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const SchedConst &sc, const double *t_dev,
-                              double t_off, int64_t nstage, StageFGE *out, unsigned *status, cudaStream_t st)
+int uniform_law(const hfs_instance *inst, int64_t count)
 {
-    const int64_t n = count * nstage;
-    if (n == 0) return cudaSuccess;
-    stage_flow_kernel<<<blocks_for(n, 128), 128, 0, st>>>(inst, count, dim, sc, t_dev, t_off, nstage, out, status);
+    if (count < 1) return -1;
+    for (int64_t i = 1; i < count; ++i)
+        if (inst[i].omega_law != inst[0].omega_law) return -1;
+    return inst[0].omega_law;
+}
+
+template <int FLOW>
+static void launch_stage_flow_law(int law, dim3 grid, const DevInst *inst, int dim, const SchedConst &sc,
+                                  const double *t_dev, double t_off, int nsteps, StageFGE *out, unsigned *status,
+                                  cudaStream_t st)
+{
+#define HFS_SF(L) stage_flow_kernel<FLOW, L><<<grid, 128, 0, st>>>(inst, dim, sc, t_dev, t_off, nsteps, out, status)
+    switch (law) {
+    case HFS_OMEGA_CONST: HFS_SF(HFS_OMEGA_CONST); break;
+    case HFS_OMEGA_SIN: HFS_SF(HFS_OMEGA_SIN); break;
+    case HFS_OMEGA_COS_SQ: HFS_SF(HFS_OMEGA_COS_SQ); break;
+    case HFS_OMEGA_PULSE: HFS_SF(HFS_OMEGA_PULSE); break;
+    default: HFS_SF(-1); break;
+    }
+#undef HFS_SF
+}
+
+cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const SchedConst &sc, const double *t_dev,
+                              double t_off, int64_t nstage, int uniform_law, StageFGE *out, unsigned *status,
+                              cudaStream_t st)
+{
+    if (count == 0 || nstage == 0) return cudaSuccess;
+    if (nstage >= INT32_MAX || nstage % sc.m != 0 || count > INT32_MAX) return cudaErrorInvalidValue;
+    const int nsteps = (int)(nstage / sc.m);
+    const dim3 grid((unsigned)count, std::min(blocks_for(nsteps, 128), 65535u));
+    switch (sc.flow) {
+    case HFS_FLOW_LEMMA2:
+        launch_stage_flow_law<HFS_FLOW_LEMMA2>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        break;
+    case HFS_FLOW_CF4:
+        launch_stage_flow_law<HFS_FLOW_CF4>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        break;
+    default:
+        launch_stage_flow_law<HFS_FLOW_M6>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        break;
+    }
     return cudaGetLastError();
 }
 
@@ -300,13 +364,18 @@ cudaError_t launch_records1d(bool fp64, const DevInst *inst, int64_t count, cons
                              double t_off, int64_t nstage, const StageFGE *fge, void *rec, unsigned *status,
                              cudaStream_t st)
 {
-    const int64_t n = count * (nstage + 1);
-    if (fp64)
-        records1d_kernel<RecD><<<blocks_for(n, 128), 128, 0, st>>>(inst, count, sc, t_dev, t_off, nstage, fge,
-                                                                    (RecD *)rec, status);
+    if (count == 0) return cudaSuccess;
+    if (nstage >= INT32_MAX || count > INT32_MAX) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)count, std::min(blocks_for(nstage + 1, 128), 65535u));
+    const bool ho = sc.split == HFS_SPLIT_HO;
+    if (fp64 && ho)
+        records1d_kernel<RecD, HFS_SPLIT_HO><<<grid, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (RecD *)rec, status);
+    else if (fp64)
+        records1d_kernel<RecD, HFS_SPLIT_FOURIER><<<grid, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (RecD *)rec, status);
+    else if (ho)
+        records1d_kernel<RecF, HFS_SPLIT_HO><<<grid, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (RecF *)rec, status);
     else
-        records1d_kernel<RecF><<<blocks_for(n, 128), 128, 0, st>>>(inst, count, sc, t_dev, t_off, nstage, fge,
-                                                                    (RecF *)rec, status);
+        records1d_kernel<RecF, HFS_SPLIT_FOURIER><<<grid, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (RecF *)rec, status);
     return cudaGetLastError();
 }
 
@@ -314,12 +383,17 @@ cudaError_t launch_records3d(bool fp64, const DevInst *inst, const SchedConst &s
                              int64_t nstage, const StageFGE *fge, void *rec, unsigned *status, cudaStream_t st)
 {
     const int64_t n = nstage + 1;
-    if (fp64)
-        records3d_kernel<Rec3D><<<blocks_for(n, 128), 128, 0, st>>>(inst, sc, t_dev, t_off, nstage, fge,
-                                                                     (Rec3D *)rec, status);
+    if (nstage >= INT32_MAX) return cudaErrorInvalidValue;
+    const unsigned b = blocks_for(n, 128);
+    const bool ho = sc.split == HFS_SPLIT_HO;
+    if (fp64 && ho)
+        records3d_kernel<Rec3D, HFS_SPLIT_HO><<<b, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (Rec3D *)rec, status);
+    else if (fp64)
+        records3d_kernel<Rec3D, HFS_SPLIT_FOURIER><<<b, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (Rec3D *)rec, status);
+    else if (ho)
+        records3d_kernel<Rec3F, HFS_SPLIT_HO><<<b, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (Rec3F *)rec, status);
     else
-        records3d_kernel<Rec3F><<<blocks_for(n, 128), 128, 0, st>>>(inst, sc, t_dev, t_off, nstage, fge,
-                                                                     (Rec3F *)rec, status);
+        records3d_kernel<Rec3F, HFS_SPLIT_FOURIER><<<b, 128, 0, st>>>(inst, sc, t_dev, t_off, (int)nstage, fge, (Rec3F *)rec, status);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,29 @@ def test_trap_laws_and_magnus_flows(precision, tol, law, lawp, flow):
     assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
 
 
+@pytest.mark.parametrize("flow", [0, 1, 2])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_mixed_trap_laws_in_one_batch(precision, tol, flow):
+    """A batch whose instances follow different trap laws takes the schedule
+    path that reads the law per instance."""
+    need_gpu()
+    laws = [(W.OMEGA_CONST, [0.0, 0.0, 0.0]), (W.OMEGA_SIN, [0.3, 1.0, 0.2]), (W.OMEGA_COS_SQ, [0.4, 2.0, 0.0]),
+            (W.OMEGA_PULSE, [0.5, 2.0, 1.0])]
+    insts, psis = [], []
+    for k, (law, lawp) in enumerate(laws):
+        if flow == 0 and law != W.OMEGA_CONST:
+            lawp = [0.0, lawp[1], lawp[2]]  # the exact flow needs a constant trap
+        inst = W.Instance(n=[256 << (k % 2)], a=[-12.0], b=[12.0], omega_law=law, w0=0.9 + 0.2 * k, law=lawp,
+                          eps=0.05, vi_kind=W.VI_COS, vi_k=1.5, sigma=4.0, ho_flow=flow, h=0.01)
+        x = inst.x()
+        insts.append(inst)
+        psis.append((inst.w0 / math.pi) ** 0.25 * np.exp(-inst.w0 * (x - 0.3) ** 2 / 2).astype(complex))
+    steps = 100
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    outs = _run_gpu(insts, psis, steps, precision, 0.01, flow=flow)
+    assert max(O.rel_l2(o, r) for o, r in zip(outs, refs)) <= budget(tol, steps * 0.01)
+
+
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_asymmetric_box_and_mass(precision, tol):
     """A box not centred at 0 (K1, K0 terms of the chirp) and mu != 1."""
