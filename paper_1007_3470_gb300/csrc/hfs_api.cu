@@ -98,6 +98,8 @@ struct hfs_ctx_s {
     int ept[kNumSizes] = {16, 16, 16, 16, 16, 16};
     // trap law shared by every instance (HFS_OMEGA_*), -1 for a mixed batch
     int law = -1;
+    // specialised 1D step kernel (step1d_variant), -1 for the generic one
+    int variant = -1;
     std::vector<int32_t> order;  // sorted position -> instance
     std::vector<WorkItem> work;
     // schedule
@@ -281,7 +283,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
             a.ticket = ticket;
             a.status = status;
-            const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64)));
+            const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64, c->variant)));
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
             if (c->profiling && done == 0) CK(record_prof(c, 0));
             for (int64_t s0 = 0; s0 < S; s0 += per) {
@@ -290,7 +292,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
                 a.j1 = s1 * m;
                 a.final_x = (s1 == S) ? 1 : 0;
                 CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
-                CK(launch_step1d(fp64, a, grid, c->stream));
+                CK(launch_step1d(fp64, c->variant, a, grid, c->stream));
             }
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
         } else {
@@ -356,6 +358,7 @@ int hfs_create(hfs_ctx_t *out, int dim, int precision, const hfs_instance *inst,
     c->count = count;
     c->inst.assign(inst, inst + count);
     c->law = uniform_law(inst, count);
+    c->variant = (dim == 1) ? step1d_variant(inst, count) : -1;
     c->dinst.resize(count);
     c->offsets.resize(count);
     int64_t off = 0;
@@ -666,7 +669,7 @@ static int run_diag(hfs_ctx_s *c)
         a.out = dout;
         a.ticket = wptr<unsigned>(c, c->lay.ticket);
         CK(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), c->stream));
-        const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64)));
+        const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64, c->variant)));
         CK(launch_diag1d(fp64, a, grid, c->stream));
     } else {
         Diag3DArgs a{};

@@ -184,7 +184,8 @@ extern "C" int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *
     int dev = 0, sms = 0;
     HFS_NA_CK(cudaGetDevice(&dev));
     HFS_NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = std::max(1, std::min(nwork, sms * step1d_ctas_per_sm(fp64)));
+    const int variant = step1d_variant(inst, count);
+    const int grid = std::max(1, std::min(nwork, sms * step1d_ctas_per_sm(fp64, variant)));
     for (int64_t done = 0; done < nsteps; done += kNoAllocChunk) {
         const int64_t S = std::min<int64_t>(kNoAllocChunk, nsteps - done);
         const int64_t nstage = S * sc.m;
@@ -207,7 +208,7 @@ extern "C" int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *
         a.ticket = ticket;
         a.status = status;
         HFS_NA_CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
-        HFS_NA_CK(launch_step1d(fp64, a, grid, st));
+        HFS_NA_CK(launch_step1d(fp64, variant, a, grid, st));
     }
     if (wait) {
         unsigned h_status = 0;

@@ -56,8 +56,11 @@ struct Step1DArgs {
     unsigned *ticket;
     unsigned *status;
 };
-cudaError_t launch_step1d(bool fp64, const Step1DArgs &a, int grid, cudaStream_t st);
-int step1d_ctas_per_sm(bool fp64);
+// variant: HFS_VI_* when every instance has that perturbation kind and a box
+// symmetric about 0 (FP32 only; from step1d_variant), -1 for the generic kernel
+cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st);
+int step1d_ctas_per_sm(bool fp64, int variant);
+int step1d_variant(const hfs_instance *inst, int64_t count);
 size_t step1d_smem_bytes(bool fp64);
 
 struct Diag1DArgs {

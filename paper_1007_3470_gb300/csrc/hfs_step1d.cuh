@@ -1,0 +1,293 @@
+// hfs_step1d.cuh -- the fused, persistent 1D Hermite-Fourier split-step
+// kernel (Eq. prod-genHarmOsc) for batches of independent instances of
+// mixed grid size, shared by the translation units that instantiate it.
+//
+// One launch processes sub-stages [j0, j1) of a schedule chunk for every
+// instance: for each sub-stage the merged x-phase X_j (kick f_{j-1} + e_j,
+// B flow of Lemma 1, F-split trap) in registers, the forward FFT, the
+// kinetic phase of drift D_{j+1} (with the 1/N of the inverse transform),
+// the inverse FFT; optionally the closing X_{j1}.  The state is read once
+// and written once per launch: with j1 - j0 covering a whole call
+// (resident mode) every step stays on chip; with one step per launch
+// (streaming mode) each step is one global round trip of 2 x 8 bytes per
+// complex64 point.
+//
+// Work distribution: persistent CTAs of 256 threads take work items from a
+// global ticket counter; a work item is up to 256/T instances of one grid
+// size N (T = N/E threads per instance, E values per thread), sorted by
+// decreasing N so that the longest items start first.
+#pragma once
+
+#include "hfs_fft.cuh"
+#include "hfs_law.cuh"
+#include "hfs_phase.cuh"
+#include "hfs_sched.h"
+
+namespace hfs {
+
+template <typename R> struct RecOf;
+template <> struct RecOf<float> { using type = RecF; };
+template <> struct RecOf<double> { using type = RecD; };
+
+template <typename R> struct TeamParams {
+    R xc, dx, eps, vik, sigma;
+    int vikind;
+    bool asym;
+};
+
+template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const DevInst &p)
+{
+    TeamParams<R> tp;
+    tp.xc = (R)p.xc[0];
+    tp.dx = (R)p.dx[0];
+    tp.eps = (R)p.eps;
+    tp.vik = (R)p.vi_k;
+    tp.sigma = (R)p.sigma;
+    tp.vikind = (p.eps != 0.0) ? p.vi_kind : HFS_VI_NONE;
+    tp.asym = (p.xc[0] != 0.0);
+    return tp;
+}
+
+// Opaque dependence on a group of register values: work on later groups
+// cannot be scheduled before this point, so the phase loops below keep one
+// group of PHASE_GROUP elements in flight instead of interleaving all E.
+#ifndef HFS_PHASE_GROUP
+#define HFS_PHASE_GROUP 4
+#endif
+constexpr int PHASE_GROUP = HFS_PHASE_GROUP;
+// Phase arithmetic of point pairs in packed FP32 instructions for plans with
+// at least this many values per thread (all plans; measured 2-5 % faster
+// than the scalar form for both 8 and 16 values per thread).
+#ifndef HFS_PACK_PHASE_MIN_E
+#define HFS_PACK_PHASE_MIN_E 8
+#endif
+template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
+{
+#ifndef HFS_NO_PHASE_FENCE
+#pragma unroll
+    for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+f"(v[e].x), "+f"(v[e].y));
+#endif
+}
+template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E], int e0)
+{
+#pragma unroll
+    for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+d"(v[e].x), "+d"(v[e].y));
+}
+
+// merged x-phase X_j on the register layout (position t + T e)
+// the phase argument of one point (turns) before the B-flow term
+template <int VI>
+__device__ __forceinline__ float xphase_F(cpx<float> u, float mf, const TeamParams<float> &tp)
+{
+    const float dens = u.x * u.x + u.y * u.y;
+    if constexpr (VI == HFS_VI_NONE) {
+        return tp.sigma * dens;
+    } else {
+        const float x = VI < 0 ? fmaf(mf, tp.dx, tp.xc) : mf * tp.dx;
+        return fmaf(tp.sigma, dens, tp.eps * vi_eval(VI < 0 ? tp.vikind : VI, x, tp.vik));
+    }
+}
+
+// VI >= 0: every instance of the launch has the perturbation kind VI and a
+// box symmetric about 0 (compile-time, no per-point tests); VI = -1: both
+// read from the team's instance.  Run-time tests inside the unrolled loop
+// were evaluated for every point, both branches (7 % of the kernel time).
+template <int N, int E, int VI>
+__device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp)
+{
+    constexpr int T = N / E;
+    constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
+    static_assert(E % 2 == 0 && PHASE_GROUP % 2 == 0, "points are phased in pairs");
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+        if (e % PHASE_GROUP == 0) fence_group(v, e);
+        const int m0 = t + T * e - N / 2, m1 = m0 + T;
+        const float2 mf = make_float2((float)m0, (float)m1);
+        float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.k2hi, rc.k2lo);
+        if (VI < 0 && tp.asym) {
+            const float2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
+            turns = make_float2(turns.x + (lin.x + rc.k0), turns.y + (lin.y + rc.k0));
+        }
+        const float2 F = make_float2(xphase_F<VI>(v[e], mf.x, tp), xphase_F<VI>(v[e + 1], mf.y, tp));
+        if constexpr (PK) turns = __ffma2_rn(bc2(rc.sb2pi), F, turns);
+        else turns = make_float2(fmaf(rc.sb2pi, F.x, turns.x), fmaf(rc.sb2pi, F.y, turns.y));
+        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f);
+    }
+}
+
+template <int N, int E, int VI>
+__device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &rc, const TeamParams<double> &tp)
+{
+    constexpr int T = N / E;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int m = t + T * e - N / 2;
+        const double mf = (double)m;
+        double turns = frac_turns(mf * mf, rc.k2, 0.0);
+        if (tp.asym) turns += frac_turns(mf, rc.k1, 0.0) + rc.k0;
+        const double x = fma(mf, tp.dx, tp.xc);
+        const double dens = v[e].x * v[e].x + v[e].y * v[e].y;
+        const double F = fma(tp.sigma, dens, tp.eps * vi_eval(tp.vikind, x, tp.vik));
+        turns = fma(rc.sb2pi, F, turns);
+        v[e] = apply_turns(v[e], turns, 1.0);
+    }
+}
+
+// kinetic phase of drift D_{j+1} with the inverse transform's 1/N
+template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E], int t, const RecF &rc)
+{
+    constexpr int T = N / E;
+    constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+        if (e % PHASE_GROUP == 0) fence_group(v, e);
+        const int k0 = t + T * e, k1 = k0 + T;
+        const int m0 = (k0 < N / 2) ? k0 : k0 - N;
+        const int m1 = (k1 < N / 2) ? k1 : k1 - N;
+        const float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.ghi, rc.glo);
+        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f / N);
+    }
+}
+
+template <int N, int E> __device__ __forceinline__ void kphase(cpx<double> (&v)[E], int t, const RecD &rc)
+{
+    constexpr int T = N / E;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + T * e;
+        const double m = (double)((k < N / 2) ? k : k - N);
+        const double turns = frac_turns(m * m, rc.g, 0.0);
+        v[e] = apply_turns(v[e], turns, 1.0 / N);
+    }
+}
+
+template <typename R, int VI, int N, int E>
+__device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
+{
+    using Rec = typename RecOf<R>::type;
+    constexpr int T = N / E;
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const bool active = g < it.count;
+    const int idx = a.order[it.first + (active ? g : 0)];
+    const DevInst &ip = a.inst[idx];
+    const TeamParams<R> tp = team_params<R>(ip);
+    cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + ip.off;
+    cpx<R> *sm = smem + g * smem_elems(N);
+    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
+    const Rec *rec = reinterpret_cast<const Rec *>(a.rec) + (int64_t)idx * a.nrec;
+
+    cpx<R> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = active ? psi[t + T * e] : cpx<R>{R(0), R(0)};
+
+    for (int64_t j = a.j0; j < a.j1; ++j) {
+        const Rec rc = rec[j];
+        // Position-dependent values (m^2, x, V_I(x)) are the same at every
+        // step; an opaque copy of t makes the compiler recompute them (a few
+        // integer and SFU operations) instead of holding 3E of them live
+        // across the whole time loop.
+        int tl = t;
+#ifndef HFS_NO_STEP_LAUNDER
+        asm volatile("" : "+r"(tl));
+#endif
+        xphase<N, E, VI>(v, tl, rc, tp);
+        FftPlan<N, E>::template run<false, R>(v, sm, tl, tw);
+        kphase<N, E>(v, tl, rc);
+        FftPlan<N, E>::template run<true, R>(v, sm, tl, tw);
+    }
+    if (a.final_x) {
+        const Rec rc = rec[a.j1];
+        xphase<N, E, VI>(v, t, rc, tp);
+    }
+    if (active) {
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            psi[t + T * e] = v[e];
+            bad |= !(isfinite(v[e].x) && isfinite(v[e].y));
+        }
+        if (bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    }
+}
+
+#ifdef HFS_ONLY_EPT8
+#define HFS_FOR_EACH_PLAN(X) X(2048, 8) X(1024, 8) X(512, 8) X(256, 8) X(128, 8)
+#else
+#define HFS_FOR_EACH_PLAN(X)                                                                                      \
+    X(4096, 16) X(2048, 16) X(1024, 16) X(512, 16) X(256, 16) X(128, 16) X(2048, 8) X(1024, 8) X(512, 8)        \
+        X(256, 8) X(128, 8)
+#endif
+
+// FP32: two CTAs per SM (128 registers); FP64 parity mode: one
+#ifndef HFS_STEP1D_MIN_CTAS
+#define HFS_STEP1D_MIN_CTAS 2
+#endif
+template <typename R> struct MinCtas { static constexpr int value = sizeof(R) == 4 ? HFS_STEP1D_MIN_CTAS : 1; };
+
+template <typename R, int VI>
+__global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(const Step1DArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<R> *smem = reinterpret_cast<cpx<R> *>(smem_raw);
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const int w = s_item;
+        if (w >= a.nwork) break;
+        const WorkItem it = a.work[w];
+        switch (it.plan) {
+#define HFS_CASE(NN, EE)                                                                                          \
+    case plan_id(NN, EE):                                                                                         \
+        step_item<R, VI, NN, EE>(a, it, smem);                                                                    \
+        break;
+            HFS_FOR_EACH_PLAN(HFS_CASE)
+#undef HFS_CASE
+        default:
+            if (threadIdx.x == 0) atomicOr(a.status, (unsigned)ST_BADPLAN);
+        }
+        __syncthreads();
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// per-variant host launch (instantiated in one translation unit per variant)
+// ---------------------------------------------------------------------------
+size_t step1d_smem_bytes(bool fp64);
+
+template <typename R, int VI> cudaError_t step1d_prepare_t()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(step1d_kernel<R, VI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)step1d_smem_bytes(sizeof(R) == 8));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <typename R, int VI> int step1d_ctas_per_sm_t()
+{
+    if (step1d_prepare_t<R, VI>() != cudaSuccess) return 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step1d_kernel<R, VI>, kCtaThreads,
+                                                                        step1d_smem_bytes(sizeof(R) == 8));
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+template <typename R, int VI> cudaError_t step1d_launch_t(const Step1DArgs &a, int grid, cudaStream_t st)
+{
+    const cudaError_t e = step1d_prepare_t<R, VI>();
+    if (e != cudaSuccess) return e;
+    step1d_kernel<R, VI><<<grid, kCtaThreads, step1d_smem_bytes(sizeof(R) == 8), st>>>(a);
+    return cudaGetLastError();
+}
+
+// explicit instantiations: the generic kernels in hfs_step1d.cu, one
+// specialised FP32 kernel per perturbation kind in hfs_step1d_vi*.cu
+#define HFS_STEP1D_VARIANT(EXTERN, R, VI)                                                                         \
+    EXTERN template cudaError_t step1d_launch_t<R, VI>(const Step1DArgs &, int, cudaStream_t);                 \
+    EXTERN template int step1d_ctas_per_sm_t<R, VI>();
+
+}  // namespace hfs

@@ -115,6 +115,28 @@ def test_mixed_trap_laws_in_one_batch(precision, tol, flow):
 
 
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_mixed_perturbations_and_boxes_in_one_batch(precision, tol):
+    """Instances with different perturbation kinds (cos, x^4, none) and a
+    shifted box in one batch run the generic step kernel; batches uniform in
+    both run a specialised one.  Both agree with the oracle."""
+    need_gpu()
+    specs = [dict(vi_kind=W.VI_COS, eps=0.05, a=[-12.0], b=[12.0]), dict(vi_kind=W.VI_X4, eps=0.002, a=[-12.0], b=[12.0]),
+             dict(vi_kind=W.VI_COS, eps=0.0, a=[-12.0], b=[12.0]), dict(vi_kind=W.VI_COS, eps=0.05, a=[-10.0], b=[14.0])]
+    insts, psis = [], []
+    for k, sp in enumerate(specs):
+        inst = W.Instance(n=[256 << (k % 3)], omega_law=W.OMEGA_SIN, w0=1.0 + 0.1 * k, law=[0.3, 1.0, 0.0], vi_k=1.5,
+                          sigma=4.0, ho_flow=1, h=0.01, **sp)
+        x = inst.x()
+        insts.append(inst)
+        psis.append((inst.w0 / math.pi) ** 0.25 * np.exp(-inst.w0 * (x - 0.4) ** 2 / 2).astype(complex))
+    steps = 100
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    for sub in (slice(0, 4), slice(0, 1), slice(1, 2), slice(2, 3)):  # generic, then uniform batches
+        outs = _run_gpu(insts[sub], psis[sub], steps, precision, 0.01)
+        assert max(O.rel_l2(o, r) for o, r in zip(outs, refs[sub])) <= budget(tol, steps * 0.01)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_asymmetric_box_and_mass(precision, tol):
     """A box not centred at 0 (K1, K0 terms of the chirp) and mu != 1."""
     need_gpu()
