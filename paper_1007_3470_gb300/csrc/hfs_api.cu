@@ -305,6 +305,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
             a.status = status;
             a.n = c->inst[0].n[0];
+            a.vi = c->inst[0].eps != 0.0 ? c->inst[0].vi_kind : HFS_VI_NONE;
             if (c->profiling && done == 0) CK(record_prof(c, 0));
             CK(launch_step3d(fp64, a, c->stream));
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));

@@ -30,8 +30,8 @@ __device__ __forceinline__ double frac_turns(double m2, double c, double /*unuse
 }
 
 // u * exp(-2 pi i turns) * scale (FP32).
-// The quarter turn q = rint(4r) of r = turns mod 1 is split off exactly,
-// leaving theta = 2 pi (r - q/4) with |theta| <= pi/4, where sin is the
+// The quarter turn q = rint(4 turns) is split off exactly (only q mod 4
+// matters), leaving theta = 2 pi (turns - q/4) with |theta| <= pi/4, where sin is the
 // Taylor series to theta^9 and cos - 1 the series to theta^10 (truncation
 // below 2e-9).  The small rotation is applied as u + u (cos - 1 - i sin):
 // rounding cos theta itself to FP32 would return exactly 1 for
@@ -41,9 +41,10 @@ __device__ __forceinline__ double frac_turns(double m2, double c, double /*unuse
 // quarter turn (-i)^q is then an exact swap / negation.
 __device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, float scale)
 {
-    const float r = turns - rintf(turns);
-    const float q = rintf(4.0f * r);
-    const float f = fmaf(q, -0.25f, r);  // exact
+    // rint(4 turns) and turns - q/4 are exact: the same quarter turn mod 4 and
+    // remainder as after a reduction of turns mod 1
+    const float q = rintf(4.0f * turns);
+    const float f = fmaf(q, -0.25f, turns);  // exact
     const float th = f * 6.28318530717958647692f;
     const float t2 = th * th;
     float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
@@ -86,11 +87,12 @@ template <bool PK> __device__ __forceinline__ float2 frac_turns2(float2 m2, floa
 
 // the small-rotation part of apply_turns for two points: quarter turns q,
 // sin theta and cos theta - 1
+// (no separate reduction mod 1: rint(4 turns) and turns - q/4 are exact and
+// give the same quarter turn mod 4 and the same remainder as after one)
 __device__ __forceinline__ void small_rotation2(float2 turns, float2 &q, float2 &sn, float2 &cm1)
 {
-    const float2 r = __fadd2_rn(turns, neg2(rint2(turns)));
-    q = rint2(__fmul2_rn(bc2(4.0f), r));
-    const float2 f = __ffma2_rn(q, bc2(-0.25f), r);
+    q = rint2(__fmul2_rn(bc2(4.0f), turns));
+    const float2 f = __ffma2_rn(q, bc2(-0.25f), turns);
     const float2 th = __fmul2_rn(f, bc2(6.28318530717958647692f));
     const float2 t2 = __fmul2_rn(th, th);
     float2 ps = __ffma2_rn(t2, bc2(1.0f / 362880.0f), bc2(-1.0f / 5040.0f));

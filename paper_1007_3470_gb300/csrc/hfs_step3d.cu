@@ -136,11 +136,23 @@ template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpas
         const int my = (y < N / 2) ? y : y - N;
         const R txy = turns_q(mx, rc.g[0], rc.glo[0]) + turns_q(my, rc.g[1], rc.glo[1]);
         const R scale = R(1) / (R(N) * R(N) * R(N));
+        if constexpr (sizeof(R) == 4) {
+            // points in pairs, the phase arithmetic in packed FP32 (bit-identical)
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int kz = t + T * e;
-            const int mz = (kz < N / 2) ? kz : kz - N;
-            v[e] = apply_turns(v[e], txy + turns_q(mz, rc.g[2], rc.glo[2]), scale);
+            for (int e = 0; e < E; e += 2) {
+                const int kz0 = t + T * e, kz1 = kz0 + T;
+                const int mz0 = (kz0 < N / 2) ? kz0 : kz0 - N, mz1 = (kz1 < N / 2) ? kz1 : kz1 - N;
+                const float2 tz = frac_turns2<true>(make_float2((float)(mz0 * mz0), (float)(mz1 * mz1)), rc.g[2],
+                                                    rc.glo[2]);
+                apply_turns2<true>(v[e], v[e + 1], __fadd2_rn(bc2(txy), tz), scale);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int kz = t + T * e;
+                const int mz = (kz < N / 2) ? kz : kz - N;
+                v[e] = apply_turns(v[e], txy + turns_q(mz, rc.g[2], rc.glo[2]), scale);
+            }
         }
     }
     FftPlan<N, E>::template run<true, R, TX>(v, sm, t, tw);
@@ -158,7 +170,10 @@ template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpas
 enum : int { P_INV_Y = 1, P_INV_X = 2, P_PHASE = 4, P_FWD_X = 8, P_FWD_Y = 16 };
 constexpr int kPlaneN = 128, kPlaneRow = kPlaneN + kPlaneN / 16, kPlaneThreads = 512;
 
-template <int MODE> __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, int64_t j)
+// VI: the instance's perturbation kind, a template parameter so that the
+// phase loop carries no per-point test of it
+template <int MODE, int VI>
+__global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, int64_t j)
 {
     constexpr int N = kPlaneN, E = 16, T = N / E, LINES = kPlaneThreads / T;  // 64 lines per round
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -189,7 +204,7 @@ template <int MODE> __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(
         const DevInst &ip = *a.inst;
         const Rec3F rc = reinterpret_cast<const Rec3F *>(a.rec)[j];
         const int mz = z - N / 2;
-        const int vkind = (ip.eps != 0.0) ? ip.vi_kind : HFS_VI_NONE;
+        constexpr int vkind = VI;
         const float dx = (float)ip.dx[0], vk = (float)ip.vi_k, eps = (float)ip.eps, sig = (float)ip.sigma;
         const float tz = turns_q(mz, rc.k2[2], rc.k2lo[2]);
         const float vz = vi_eval(vkind, (float)mz * (float)ip.dx[2], vk);
@@ -204,14 +219,19 @@ template <int MODE> __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(
                 const int my = y - N / 2;
                 const float tyz = turns_q(my, rc.k2[1], rc.k2lo[1]) + tz;
                 const float vyz = vi_eval(vkind, (float)my * (float)ip.dx[1], vk) + vz;
+                // points in pairs, the phase arithmetic in packed FP32 (bit-identical)
+                auto Fof = [&](const cpx<float> &u, int mx) {
+                    const float dens = u.x * u.x + u.y * u.y;
+                    return sig * dens + eps * (vi_eval(vkind, (float)mx * dx, vk) + vyz);
+                };
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int mx = t + T * e - N / 2;
-                    float turns = turns_q(mx, rc.k2[0], rc.k2lo[0]) + tyz;
-                    const float dens = v[e].x * v[e].x + v[e].y * v[e].y;
-                    const float F = sig * dens + eps * (vi_eval(vkind, (float)mx * dx, vk) + vyz);
-                    turns += rc.sb2pi * F;
-                    v[e] = apply_turns(v[e], turns, 1.0f);
+                for (int e = 0; e < E; e += 2) {
+                    const int mx0 = t + T * e - N / 2, mx1 = mx0 + T;
+                    float2 turns = frac_turns2<true>(make_float2((float)(mx0 * mx0), (float)(mx1 * mx1)), rc.k2[0],
+                                                     rc.k2lo[0]);
+                    turns = __fadd2_rn(turns, bc2(tyz));
+                    turns = __ffma2_rn(bc2(rc.sb2pi), make_float2(Fof(v[e], mx0), Fof(v[e + 1], mx1)), turns);
+                    apply_turns2<true>(v[e], v[e + 1], turns, 1.0f);
                 }
             }
             if constexpr (MODE & P_FWD_X) FftPlan<N, E>::template run<false, float>(v, row, t, tw);
@@ -408,30 +428,40 @@ template <typename R, int N> static cudaError_t diag3d(const Diag3DArgs &a, cuda
     return cudaGetLastError();
 }
 
-static cudaError_t run3d_plane(const Step3DArgs &a, cudaStream_t st)
+template <int VI> static cudaError_t run3d_plane_vi(const Step3DArgs &a, cudaStream_t st)
 {
     constexpr int N = kPlaneN;
     using GEO = Geo3<N>;
+    constexpr int FIRST = P_PHASE | P_FWD_X | P_FWD_Y, MID = P_INV_Y | P_INV_X | P_PHASE | P_FWD_X | P_FWD_Y,
+                  LAST = P_INV_Y | P_INV_X | P_PHASE;
     const size_t ps = (size_t)N * kPlaneRow * sizeof(cpx<float>), ts = tsmem<float, N>();
     static bool prepared = false;
     if (!prepared) {
         cudaError_t e;
-        if ((e = allow_smem(plane3d<P_PHASE | P_FWD_X | P_FWD_Y>, ps)) != cudaSuccess) return e;
-        if ((e = allow_smem(plane3d<P_INV_Y | P_INV_X | P_PHASE | P_FWD_X | P_FWD_Y>, ps)) != cudaSuccess) return e;
-        if ((e = allow_smem(plane3d<P_INV_Y | P_INV_X | P_PHASE>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<FIRST, VI>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<MID, VI>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<LAST, VI>, ps)) != cudaSuccess) return e;
         if ((e = allow_smem(zpass3d<float, N>, ts)) != cudaSuccess) return e;
         prepared = true;
     }
     const dim3 tg(N / GEO::TX, N);
-    plane3d<P_PHASE | P_FWD_X | P_FWD_Y><<<N, kPlaneThreads, ps, st>>>(a, 0);
+    plane3d<FIRST, VI><<<N, kPlaneThreads, ps, st>>>(a, 0);
     for (int64_t j = 0; j < a.nstage; ++j) {
         zpass3d<float, N><<<tg, GEO::TT, ts, st>>>(a, j);
-        if (j + 1 < a.nstage)
-            plane3d<P_INV_Y | P_INV_X | P_PHASE | P_FWD_X | P_FWD_Y><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
-        else
-            plane3d<P_INV_Y | P_INV_X | P_PHASE><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+        if (j + 1 < a.nstage) plane3d<MID, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+        else plane3d<LAST, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
     }
     return cudaGetLastError();
+}
+
+static cudaError_t run3d_plane(const Step3DArgs &a, cudaStream_t st)
+{
+    switch (a.vi) {
+    case HFS_VI_COS: return run3d_plane_vi<HFS_VI_COS>(a, st);
+    case HFS_VI_X4: return run3d_plane_vi<HFS_VI_X4>(a, st);
+    case HFS_VI_NONE: return run3d_plane_vi<HFS_VI_NONE>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_step3d(bool fp64, const Step3DArgs &a, cudaStream_t st)

@@ -13,7 +13,8 @@ struct Step3DArgs {
     int64_t nstage;
     const void *tw;
     unsigned *status;
-    int n;  // points per axis
+    int n;   // points per axis
+    int vi;  // perturbation kind in effect (HFS_VI_NONE where eps = 0)
 };
 
 struct Diag3DArgs {
