@@ -181,8 +181,13 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
     const auto *tw = reinterpret_cast<const float4 *>(a.tw);
-    // load the plane: element (y, x) -> row y, padded slot of x
-    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) pl[(i / N) * kPlaneRow + spad(i % N)] = psi[i];
+    // load the plane: element (y, x) -> row y, padded slot of x, by
+    // asynchronous 8-byte copies (all in flight at once, no registers held)
+    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(pl + (i / N) * kPlaneRow + spad(i % N));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + i) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     cpx<float> v[E];
     if constexpr (MODE & P_INV_Y) {
