@@ -115,7 +115,11 @@ __global__ void __launch_bounds__(kCtaThreads) ypass3d(const Step3DArgs a)
 // z-pass: one CTA = fixed y, TX adjacent x columns; forward FFT_z, k-phase,
 // inverse FFT_z
 // ---------------------------------------------------------------------------
-template <typename R, int N> __global__ void __launch_bounds__(kCtaThreads) zpass3d(const Step3DArgs a, int64_t j)
+// FP32: two CTAs per SM (128 registers; at 143 registers one CTA of 8 warps
+// per SM left the column loads' latency exposed); FP64: one
+template <typename R> struct ZpassMinCtas { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
+template <typename R, int N>
+__global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(const Step3DArgs a, int64_t j)
 {
     using Rec = typename Rec3Of<R>::type;
     using GEO = Geo3<N>;
@@ -181,23 +185,27 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
     const auto *tw = reinterpret_cast<const float4 *>(a.tw);
-    // load the plane: element (y, x) -> row y, padded slot of x, by
-    // asynchronous 8-byte copies (all in flight at once, no registers held)
-    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(pl + (i / N) * kPlaneRow + spad(i % N));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + i) : "memory");
+    // With the inverse y-transform the columns come straight from global
+    // memory (lanes are adjacent x: coalesced); otherwise the plane is loaded
+    // into shared memory (row y, padded slot of x) by asynchronous 8-byte
+    // copies, all in flight at once.
+    if constexpr (!(MODE & P_INV_Y)) {
+        for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(pl + (i / N) * kPlaneRow + spad(i % N));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + i) : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
     cpx<float> v[E];
     if constexpr (MODE & P_INV_Y) {
         // columns: lanes are adjacent x, slots of a column are kPlaneRow apart
         const int l = threadIdx.x % LINES, t = threadIdx.x / LINES;
         for (int r = 0; r < N / LINES; ++r) {
-            cpx<float> *col = pl + spad(r * LINES + l);
+            const int x = r * LINES + l;
+            cpx<float> *col = pl + spad(x);
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = col[(t + T * e) * kPlaneRow];
-            __syncthreads();
+            for (int e = 0; e < E; ++e) v[e] = psi[(t + T * e) * N + x];
             FftPlan<N, E>::template run<true, float, kPlaneRow>(v, col, t, tw);
 #pragma unroll
             for (int e = 0; e < E; ++e) col[(t + T * e) * kPlaneRow] = v[e];
@@ -245,24 +253,26 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
             __syncthreads();
         }
     }
+    bool bad = false;
     if constexpr (MODE & P_FWD_Y) {
+        // the forward y-transform writes its columns straight to global memory
         const int l = threadIdx.x % LINES, t = threadIdx.x / LINES;
         for (int r = 0; r < N / LINES; ++r) {
-            cpx<float> *col = pl + spad(r * LINES + l);
+            const int x = r * LINES + l;
+            cpx<float> *col = pl + spad(x);
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = col[(t + T * e) * kPlaneRow];
             __syncthreads();
             FftPlan<N, E>::template run<false, float, kPlaneRow>(v, col, t, tw);
 #pragma unroll
-            for (int e = 0; e < E; ++e) col[(t + T * e) * kPlaneRow] = v[e];
-            __syncthreads();
+            for (int e = 0; e < E; ++e) psi[(t + T * e) * N + x] = v[e];
         }
-    }
-    bool bad = false;
-    for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
-        const cpx<float> w = pl[(i / N) * kPlaneRow + spad(i % N)];
-        psi[i] = w;
-        bad |= !(isfinite(w.x) && isfinite(w.y));
+    } else {
+        for (int i = threadIdx.x; i < N * N; i += kPlaneThreads) {
+            const cpx<float> w = pl[(i / N) * kPlaneRow + spad(i % N)];
+            psi[i] = w;
+            bad |= !(isfinite(w.x) && isfinite(w.y));
+        }
     }
     if ((MODE & P_PHASE) && !(MODE & P_FWD_X) && bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
 }
