@@ -60,3 +60,22 @@ def test_3d_chunked_equals_oracle():
     ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
     out, _, _ = _gpu3d(inst, psi0, steps, "c128", chunk=4)
     assert O.rel_l2(out, ref) <= budget(TOL_C128, steps * inst.h)
+
+
+@pytest.mark.parametrize("vi_kind,eps", [(W.VI_X4, 2e-5), (W.VI_NONE, 0.05), (W.VI_COS, 0.0)])
+def test_3d_128_plane_kernels_per_perturbation(vi_kind, eps):
+    """The 128^3 complex64 plane kernel is compiled per perturbation kind in
+    effect (x^4; none; cos with eps = 0 is none); each agrees with the FP64
+    line-pass path and with the oracle."""
+    need_gpu()
+    import dataclasses
+    inst, psi0, _ = W.gpe_3d(n=128, h=0.005)
+    inst = dataclasses.replace(inst, vi_kind=vi_kind, eps=eps)
+    steps = 4
+    o32, n32, _ = _gpu3d(inst, psi0, steps, "c64")
+    o64, _, _ = _gpu3d(inst, psi0, steps, "c128")
+    T = steps * inst.h
+    assert O.rel_l2(o32, o64) <= TOL_C64 * max(T, 1.0) * 0.1
+    assert abs(n32 - 1.0) < 3e-6
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    assert O.rel_l2(o64, ref) <= TOL_C128 * max(T, 1.0)
