@@ -80,7 +80,7 @@ double omega_bound(const hfs_instance &p, double t0, double t1)
 namespace {
 
 struct Layout {
-    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, rec, diag, total;
+    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, nodes, rec, diag, total;
 };
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -96,8 +96,10 @@ struct hfs_ctx_s {
     int64_t elems = 0;
     // 1D plans: elements per thread per size class
     int ept[kNumSizes] = {16, 16, 16, 16, 16, 16};
-    // trap law shared by every instance (HFS_OMEGA_*), -1 for a mixed batch
+    // trap law shared by every instance (HFS_OMEGA_*), -1 for a mixed batch,
+    // and whether its parameters are shared too
     int law = -1;
+    bool law_shared = false;
     // specialised 1D step kernel (step1d_variant), -1 for the generic one
     int variant = -1;
     std::vector<int32_t> order;  // sorted position -> instance
@@ -169,6 +171,7 @@ Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
     L.twf = take(sizeof(float4) * kTwiddleTotal);
     L.twd = take(sizeof(cpx<double>) * kTwiddleTotal);
     L.fge = take(sizeof(StageFGE) * c->count * nstage * c->dim);
+    L.nodes = take(law_nodes_bytes(nstage));
     L.rec = take(recsz * c->count * (nstage + 1));
     L.diag = take(sizeof(double) * 2 * std::max<int64_t>(c->count, 1));
     L.total = o;
@@ -269,7 +272,8 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
         const int64_t nstage = S * m;
         const double toff = (double)done * c->sc.h;
         if (c->sc.split == HFS_SPLIT_HO)
-            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, c->law, fge, status, c->stream));
+            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, c->law, c->law_shared,
+                                 wptr<void>(c, c->lay.nodes), fge, status, c->stream));
         if (c->dim == 1) {
             CK(launch_records1d(fp64, dinst, c->count, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
             Step1DArgs a{};
@@ -359,6 +363,7 @@ int hfs_create(hfs_ctx_t *out, int dim, int precision, const hfs_instance *inst,
     c->count = count;
     c->inst.assign(inst, inst + count);
     c->law = uniform_law(inst, count);
+    c->law_shared = law_shared(inst, count);
     c->variant = (dim == 1) ? step1d_variant(inst, count) : -1;
     c->dinst.resize(count);
     c->offsets.resize(count);

@@ -1,4 +1,9 @@
 // hfs_law.cuh -- the trap law omega^2(t) of Eq. GP1b (device, FP64).
+//
+// Every law is omega^2(t) = omega0^2 S(t) with a shape factor S that depends
+// only on the law and its parameters: a batch whose instances share those
+// evaluates S once per time node (law_factor*), each instance multiplies by
+// its own omega0^2 (and the axis scale^2 in 3D).
 #pragma once
 
 #include "hfs_internal.cuh"
@@ -7,25 +12,30 @@ namespace hfs {
 
 // LAW >= 0: the law is known at compile time (every instance of a batch uses
 // it); LAW = -1 reads it from the instance
-template <int LAW = -1> __device__ __forceinline__ double law_omega2(const DevInst &p, double t)
+template <int LAW = -1> __device__ __forceinline__ double law_factor(const DevInst &p, double t)
 {
-    double w;
+    double u;
     switch (LAW >= 0 ? LAW : p.omega_law) {
     case HFS_OMEGA_CONST:
-        return p.w0 * p.w0;
-    case HFS_OMEGA_SIN:
-        w = p.w0 * (1.0 + p.law[0] * sin(fma(p.law[1], t, p.law[2])));
-        return w * w;
-    case HFS_OMEGA_COS_SQ:
-        return p.w0 * p.w0 * (1.0 + p.law[0] * cos(p.law[1] * t));
-    case HFS_OMEGA_PULSE: {
+        return 1.0;
+    case HFS_OMEGA_SIN:  // omega = omega0 (1 + A sin(W t + phi))
+        u = 1.0 + p.law[0] * sin(fma(p.law[1], t, p.law[2]));
+        return u * u;
+    case HFS_OMEGA_COS_SQ:  // omega^2 = omega0^2 (1 + A cos(W t))
+        return 1.0 + p.law[0] * cos(p.law[1] * t);
+    case HFS_OMEGA_PULSE: {  // omega = omega0 (1 + A t / cosh^2(B (t - t_c)))
         const double ch = cosh(p.law[1] * (t - p.law[2]));
-        w = p.w0 * (1.0 + p.law[0] * t / (ch * ch));
-        return w * w;
+        u = 1.0 + p.law[0] * t / (ch * ch);
+        return u * u;
     }
     default:
         return nan("");
     }
+}
+
+template <int LAW = -1> __device__ __forceinline__ double law_omega2(const DevInst &p, double t)
+{
+    return p.w0 * p.w0 * law_factor<LAW>(p, t);
 }
 
 template <int LAW = -1> __device__ __forceinline__ double axis_omega2(const DevInst &p, int dim, int axis, double t)
@@ -47,35 +57,31 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c)
     }
 }
 
-// omega^2 at the two symmetric nodes tm - d and tm + d (the Gauss nodes of a
+// S at the two symmetric nodes tm - d and tm + d (the Gauss nodes of a
 // stage): the periodic laws take both from one sincos of the midpoint
 // argument, sin(th -+ de) = sin th cos de -+ cos th sin de
 template <int LAW = -1>
-__device__ __forceinline__ void axis_omega2_pair(const DevInst &p, int dim, int axis, double tm, double d,
-                                                 double &w1, double &w2)
+__device__ __forceinline__ void law_factor_pair(const DevInst &p, double tm, double d, double &s1, double &s2)
 {
-    const double c = (dim == 1) ? 1.0 : p.axis_scale[axis];
-    const double c2 = c * c;
     const int law = LAW >= 0 ? LAW : p.omega_law;
     if (law == HFS_OMEGA_SIN) {
         double st, ct, sd, cd;
         sincos(fma(p.law[1], tm, p.law[2]), &st, &ct);
         sincos_small(p.law[1] * d, sd, cd);
         const double a = st * cd, b = ct * sd;
-        const double u1 = p.w0 * (1.0 + p.law[0] * (a - b)), u2 = p.w0 * (1.0 + p.law[0] * (a + b));
-        w1 = c2 * (u1 * u1);
-        w2 = c2 * (u2 * u2);
+        const double u1 = 1.0 + p.law[0] * (a - b), u2 = 1.0 + p.law[0] * (a + b);
+        s1 = u1 * u1;
+        s2 = u2 * u2;
     } else if (law == HFS_OMEGA_COS_SQ) {
         double st, ct, sd, cd;
         sincos(p.law[1] * tm, &st, &ct);
         sincos_small(p.law[1] * d, sd, cd);
         const double a = ct * cd, b = st * sd;
-        const double k = p.w0 * p.w0;
-        w1 = c2 * (k * (1.0 + p.law[0] * (a + b)));
-        w2 = c2 * (k * (1.0 + p.law[0] * (a - b)));
+        s1 = 1.0 + p.law[0] * (a + b);
+        s2 = 1.0 + p.law[0] * (a - b);
     } else {
-        w1 = axis_omega2<LAW>(p, dim, axis, tm - d);
-        w2 = axis_omega2<LAW>(p, dim, axis, tm + d);
+        s1 = law_factor<LAW>(p, tm - d);
+        s2 = law_factor<LAW>(p, tm + d);
     }
 }
 

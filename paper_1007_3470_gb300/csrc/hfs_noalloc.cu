@@ -39,8 +39,8 @@ constexpr size_t kOffWork = kOffOrder + al256(sizeof(int32_t) * kNoAllocMaxInsta
 constexpr size_t kOffTwf = kOffWork + al256(sizeof(WorkItem) * kNoAllocMaxInstances);
 constexpr size_t kOffTwd = kOffTwf + al256(sizeof(float4) * kTwiddleTotal);
 constexpr size_t kOffFge = kOffTwd + al256(sizeof(double2) * kTwiddleTotal);
-constexpr size_t kOffRec =
-    kOffFge + al256(sizeof(StageFGE) * kNoAllocMaxInstances * kNoAllocChunk * kNoAllocMaxStages);
+constexpr size_t kOffNodes = kOffFge + al256(sizeof(StageFGE) * kNoAllocMaxInstances * kNoAllocChunk * kNoAllocMaxStages);
+constexpr size_t kOffRec = kOffNodes + al256(3 * sizeof(double) * kNoAllocChunk * kNoAllocMaxStages);
 constexpr size_t kRecMax = sizeof(RecD) > sizeof(RecF) ? sizeof(RecD) : sizeof(RecF);
 constexpr size_t kEnd = kOffRec + al256(kRecMax * kNoAllocMaxInstances * (kNoAllocChunk * kNoAllocMaxStages + 1));
 static_assert(kEnd <= kNoAllocBytes, "scratch layout exceeds HFS_NOALLOC_SCRATCH_BYTES");
@@ -191,7 +191,8 @@ extern "C" int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *
         const int64_t nstage = S * sc.m;
         const double toff = (double)done * dt;
         if (split == HFS_SPLIT_HO)
-            HFS_NA_CK(launch_stage_flow(dinst, count, 1, sc, tdev, toff, nstage, uniform_law(inst, count), fge, status, st));
+            HFS_NA_CK(launch_stage_flow(dinst, count, 1, sc, tdev, toff, nstage, uniform_law(inst, count),
+                                        law_shared(inst, count), base + kOffNodes, fge, status, st));
         HFS_NA_CK(launch_records1d(fp64, dinst, count, sc, tdev, toff, nstage, fge, rec, status, st));
         Step1DArgs a{};
         a.psi = psi;

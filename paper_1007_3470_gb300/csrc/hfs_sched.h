@@ -27,12 +27,17 @@ struct alignas(16) Rec3D {
     double sb2pi, pad;
 };
 
-// uniform_law: the HFS_OMEGA_* law shared by all instances, or -1 for a mixed batch
+// uniform_law: the HFS_OMEGA_* law shared by all instances, or -1 for a mixed
+// batch; shared: the law parameters are shared too (law_shared), so the trap's
+// shape factors are evaluated once per stage into `nodes` (law_nodes_bytes)
 cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const SchedConst &sc, const double *t_dev,
-                              double t_off, int64_t nstage, int uniform_law, StageFGE *out, unsigned *status,
-                              cudaStream_t st);
+                              double t_off, int64_t nstage, int uniform_law, bool shared, void *nodes,
+                              StageFGE *out, unsigned *status, cudaStream_t st);
 // the law shared by every instance of inst[0..count), or -1
 int uniform_law(const hfs_instance *inst, int64_t count);
+// every instance has the same law and law parameters
+bool law_shared(const hfs_instance *inst, int64_t count);
+size_t law_nodes_bytes(int64_t nstage);
 cudaError_t launch_records1d(bool fp64, const DevInst *inst, int64_t count, const SchedConst &sc, const double *t_dev,
                              double t_off, int64_t nstage, const StageFGE *fge, void *rec, unsigned *status,
                              cudaStream_t st);

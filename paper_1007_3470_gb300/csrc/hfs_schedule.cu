@@ -120,31 +120,54 @@ __device__ void fge_thm1(double al, double be, double ga, double s, double &f, d
     e = (r.OMC - be * r.S) * ig;
 }
 
-// FLOW (and, when a batch shares one trap law, LAW) are template parameters:
-// with a run-time flow the compiler evaluated all three branches and kept one
-// result (3.6x the FP64 work)
-template <int FLOW, int LAW>
-__device__ void stage_fge(const DevInst &p, int dim, int axis, double tau, double s, double &f, double &g, double &e)
+constexpr double kR3 = 0.28867513459481288225;   // sqrt(3)/6
+constexpr double kR15 = 0.38729833462074168852;  // sqrt(15)/10
+
+// The trap's shape factors S (omega^2 = omega0^2 S) of one stage over
+// [tau, tau + s] at the nodes its flow reads: the stage start (Lemma 2), the
+// two Gauss nodes (Magnus-4), the three Gauss nodes (Magnus-6).
+struct NodeS {
+    double s[3];
+};
+
+template <int FLOW, int LAW> __device__ __forceinline__ NodeS stage_nodes(const DevInst &p, double tau, double s)
 {
+    NodeS r{};
     if constexpr (FLOW == HFS_FLOW_LEMMA2) {
-        const double om = sqrt(axis_omega2<LAW>(p, dim, axis, tau));
+        r.s[0] = law_factor<LAW>(p, tau);
+    } else if constexpr (FLOW == HFS_FLOW_CF4) {
+        law_factor_pair<LAW>(p, tau + 0.5 * s, kR3 * s, r.s[0], r.s[1]);
+    } else {
+        law_factor_pair<LAW>(p, tau + 0.5 * s, kR15 * s, r.s[0], r.s[2]);
+        r.s[1] = law_factor<LAW>(p, tau + 0.5 * s);
+    }
+    return r;
+}
+
+// (f, g, e) of one stage on axis `axis` from the shape factors at its nodes.
+// FLOW (and LAW, SHARED below) are template parameters: with a run-time flow
+// the compiler evaluated all three branches and kept one result (3.6x the
+// FP64 work).
+template <int FLOW>
+__device__ void stage_fge(const DevInst &p, int dim, int axis, const NodeS &ns, double s, double &f, double &g,
+                          double &e)
+{
+    const double c = (dim == 1) ? 1.0 : p.axis_scale[axis];
+    const double k = c * c * (p.w0 * p.w0);  // omega^2 = k S
+    if constexpr (FLOW == HFS_FLOW_LEMMA2) {
+        const double om = sqrt(k * ns.s[0]);
         double sh, ch;
         sincos(0.5 * om * s, &sh, &ch);
         g = 2.0 * sh * ch / om;
         f = om * sh / ch;
         e = f;
     } else if constexpr (FLOW == HFS_FLOW_CF4) {
-        const double r3 = 0.28867513459481288225;  // sqrt(3)/6
-        const double al = 0.5 - 2.0 * r3;          // 1/2 - 1/sqrt(3)
+        const double al = 0.5 - 2.0 * kR3;  // 1/2 - 1/sqrt(3)
         const double be = 1.0 - al;
-        double w1, w2;
-        axis_omega2_pair<LAW>(p, dim, axis, tau + 0.5 * s, r3 * s, w1, w2);
+        const double w1 = k * ns.s[0], w2 = k * ns.s[1];
         fge_thm2(al * w1 + be * w2, be * w1 + al * w2, s, f, g, e);
     } else {
-        const double r15 = 0.38729833462074168852;  // sqrt(15)/10
-        double w1, w3;
-        axis_omega2_pair<LAW>(p, dim, axis, tau + 0.5 * s, r15 * s, w1, w3);
-        const double w2 = axis_omega2<LAW>(p, dim, axis, tau + 0.5 * s);
+        const double w1 = k * ns.s[0], w2 = k * ns.s[1], w3 = k * ns.s[2];
         const double s2 = s * s;
         const double avg = 5.0 * w1 + 8.0 * w2 + 5.0 * w3;
         const double al = avg / 18.0 + s2 / 486.0 * (4.25 * (w1 * w1 + w3 * w3) + 8.0 * w2 * w2 + w1 * w2 +
@@ -161,13 +184,27 @@ __device__ void stage_fge(const DevInst &p, int dim, int axis, double tau, doubl
     }
 }
 
+// the shape factors of every stage of the chunk, once for a batch whose
+// instances share the law and its parameters (read from instance 0)
+template <int FLOW, int LAW>
+__global__ void law_nodes_kernel(const DevInst *__restrict__ inst, SchedConst sc, const double *__restrict__ t_dev,
+                                 double t_off, int nstage, NodeS *__restrict__ nodes)
+{
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nstage) return;
+    const int n = sg / sc.m, st = sg - n * sc.m;
+    const double tau = *t_dev + t_off + (double)n * sc.h + sc.h * sc.cuma[st];
+    nodes[sg] = stage_nodes<FLOW, LAW>(inst[0], tau, sc.a[st] * sc.h);
+}
+
 // one thread per (instance, time step of the chunk), all m stages of the
 // step: instance = blockIdx.x, steps strided over blockIdx.y / threadIdx.x
-// (no 64-bit integer division in the index arithmetic)
-template <int FLOW, int LAW>
+// (no 64-bit integer division in the index arithmetic).  SHARED: the shape
+// factors come from law_nodes_kernel instead of being evaluated per instance.
+template <int FLOW, int LAW, bool SHARED>
 __global__ void stage_flow_kernel(const DevInst *__restrict__ inst, int dim, SchedConst sc,
-                                  const double *__restrict__ t_dev, double t_off, int nsteps, StageFGE *__restrict__ out,
-                                  unsigned *status)
+                                  const double *__restrict__ t_dev, double t_off, int nsteps,
+                                  const NodeS *__restrict__ nodes, StageFGE *__restrict__ out, unsigned *status)
 {
     const int64_t i = blockIdx.x;
     const DevInst p = inst[i];
@@ -178,9 +215,12 @@ __global__ void stage_flow_kernel(const DevInst *__restrict__ inst, int dim, Sch
             const double tau = t0 + (double)n * sc.h + sc.h * sc.cuma[st];
             const double s = sc.a[st] * sc.h;
             const int64_t sg = (int64_t)n * sc.m + st;
+            NodeS ns;
+            if constexpr (SHARED) ns = nodes[sg];
+            else ns = stage_nodes<FLOW, LAW>(p, tau, s);
             for (int d = 0; d < dim; ++d) {
                 double f, g, e;
-                stage_fge<FLOW, LAW>(p, dim, d, tau, s, f, g, e);
+                stage_fge<FLOW>(p, dim, d, ns, s, f, g, e);
                 if (!isfinite(f) || !isfinite(g) || !isfinite(e)) atomicOr(status, (unsigned)ST_NONFINITE);
                 StageFGE r;
                 r.f = f;
@@ -322,12 +362,42 @@ int uniform_law(const hfs_instance *inst, int64_t count)
     return inst[0].omega_law;
 }
 
-template <int FLOW>
-static void launch_stage_flow_law(int law, dim3 grid, const DevInst *inst, int dim, const SchedConst &sc,
-                                  const double *t_dev, double t_off, int nsteps, StageFGE *out, unsigned *status,
-                                  cudaStream_t st)
+bool law_shared(const hfs_instance *inst, int64_t count)
 {
-#define HFS_SF(L) stage_flow_kernel<FLOW, L><<<grid, 128, 0, st>>>(inst, dim, sc, t_dev, t_off, nsteps, out, status)
+    if (uniform_law(inst, count) < 0) return false;
+    for (int64_t i = 1; i < count; ++i)
+        for (int k = 0; k < 3; ++k)
+            if (inst[i].law[k] != inst[0].law[k]) return false;
+    return true;
+}
+
+size_t law_nodes_bytes(int64_t nstage) { return sizeof(NodeS) * (size_t)nstage; }
+
+template <int FLOW, int LAW>
+static void launch_stage_flow_fl(bool shared, dim3 grid, const DevInst *inst, int dim, const SchedConst &sc,
+                                 const double *t_dev, double t_off, int nsteps, void *nodes, StageFGE *out,
+                                 unsigned *status, cudaStream_t st)
+{
+    NodeS *nd = static_cast<NodeS *>(nodes);
+    if constexpr (LAW >= 0) {
+        if (shared && nd) {
+            const int nstage = nsteps * sc.m;
+            law_nodes_kernel<FLOW, LAW><<<blocks_for(nstage, 128), 128, 0, st>>>(inst, sc, t_dev, t_off, nstage, nd);
+            stage_flow_kernel<FLOW, LAW, true><<<grid, 128, 0, st>>>(inst, dim, sc, t_dev, t_off, nsteps, nd, out,
+                                                                      status);
+            return;
+        }
+    }
+    stage_flow_kernel<FLOW, LAW, false><<<grid, 128, 0, st>>>(inst, dim, sc, t_dev, t_off, nsteps, nullptr, out,
+                                                               status);
+}
+
+template <int FLOW>
+static void launch_stage_flow_law(int law, bool shared, dim3 grid, const DevInst *inst, int dim, const SchedConst &sc,
+                                  const double *t_dev, double t_off, int nsteps, void *nodes, StageFGE *out,
+                                  unsigned *status, cudaStream_t st)
+{
+#define HFS_SF(L) launch_stage_flow_fl<FLOW, L>(shared, grid, inst, dim, sc, t_dev, t_off, nsteps, nodes, out, status, st)
     switch (law) {
     case HFS_OMEGA_CONST: HFS_SF(HFS_OMEGA_CONST); break;
     case HFS_OMEGA_SIN: HFS_SF(HFS_OMEGA_SIN); break;
@@ -339,8 +409,8 @@ static void launch_stage_flow_law(int law, dim3 grid, const DevInst *inst, int d
 }
 
 cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const SchedConst &sc, const double *t_dev,
-                              double t_off, int64_t nstage, int uniform_law, StageFGE *out, unsigned *status,
-                              cudaStream_t st)
+                              double t_off, int64_t nstage, int uniform_law, bool shared, void *nodes,
+                              StageFGE *out, unsigned *status, cudaStream_t st)
 {
     if (count == 0 || nstage == 0) return cudaSuccess;
     if (nstage >= INT32_MAX || nstage % sc.m != 0 || count > INT32_MAX) return cudaErrorInvalidValue;
@@ -348,13 +418,16 @@ cudaError_t launch_stage_flow(const DevInst *inst, int64_t count, int dim, const
     const dim3 grid((unsigned)count, std::min(blocks_for(nsteps, 128), 65535u));
     switch (sc.flow) {
     case HFS_FLOW_LEMMA2:
-        launch_stage_flow_law<HFS_FLOW_LEMMA2>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        launch_stage_flow_law<HFS_FLOW_LEMMA2>(uniform_law, shared, grid, inst, dim, sc, t_dev, t_off, nsteps, nodes,
+                                               out, status, st);
         break;
     case HFS_FLOW_CF4:
-        launch_stage_flow_law<HFS_FLOW_CF4>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        launch_stage_flow_law<HFS_FLOW_CF4>(uniform_law, shared, grid, inst, dim, sc, t_dev, t_off, nsteps, nodes,
+                                            out, status, st);
         break;
     default:
-        launch_stage_flow_law<HFS_FLOW_M6>(uniform_law, grid, inst, dim, sc, t_dev, t_off, nsteps, out, status, st);
+        launch_stage_flow_law<HFS_FLOW_M6>(uniform_law, shared, grid, inst, dim, sc, t_dev, t_off, nsteps, nodes,
+                                           out, status, st);
         break;
     }
     return cudaGetLastError();
