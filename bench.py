@@ -50,7 +50,7 @@ STEP1D_TRAFFIC = {"src": "6327d630fa620c4b",
                   "batch_1d_4096x500_c64": 109716480 + 37320192,
                   "batch_1d_65536x1_streaming": (730917632 + 867289344 + 730905856 + 864000000) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cuh", "hfs_step1d.cu", "hfs_step1d_vicos.cu", "hfs_step1d_vix4.cu", "hfs_step1d_vinone.cu",
-                  "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_law.cuh", "hfs_sched.h")
+                  "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_sched.h")
 
 
 def step1d_traffic(workload: str):
