@@ -268,17 +268,33 @@ constexpr double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
 
 // the phase record of 1D sub-stage j (turns per integer index, see above)
+// per-instance factors of the turn coefficients: dx^2/(4 pi), xc dx/(2 pi),
+// xc^2/(4 pi), pi/L^2, h/(2 pi)
+struct RecScale {
+    double k2, k1, k0, g, sb;
+};
+__device__ __forceinline__ RecScale rec_scale(const DevInst &p, const SchedConst &sc)
+{
+    RecScale c;
+    c.k2 = p.dx[0] * p.dx[0] * kInv4Pi;
+    c.k1 = p.xc[0] * p.dx[0] * kInv2Pi;
+    c.k0 = p.xc[0] * p.xc[0] * kInv4Pi;
+    c.g = kPi / (p.len[0] * p.len[0]);
+    c.sb = sc.h * kInv2Pi;
+    return c;
+}
+
 template <typename RecT, int SPLIT>
-__device__ __forceinline__ void record1d(const DevInst &p, const SchedConst &sc, double t0, int j, int nstage,
-                                         const StageFGE *__restrict__ fge_i, RecT *out, unsigned *status)
+__device__ __forceinline__ void record1d(const DevInst &p, const SchedConst &sc, const RecScale &c, double t0, int j,
+                                         int nstage, const StageFGE *__restrict__ fge_i, RecT *out, unsigned *status)
 {
     double kappa, bs, g;
     merged_coeffs<SPLIT>(p, 1, 0, sc, t0, j, nstage, fge_i, kappa, bs, g);
-    const double K2 = kappa * p.dx[0] * p.dx[0] * kInv4Pi;
-    const double K1 = kappa * p.xc[0] * p.dx[0] * kInv2Pi;
-    const double K0 = frac1(kappa * p.xc[0] * p.xc[0] * kInv4Pi);
-    const double G = g * kPi / (p.len[0] * p.len[0]);
-    const double SB = bs * sc.h * kInv2Pi;
+    const double K2 = kappa * c.k2;
+    const double K1 = kappa * c.k1;
+    const double K0 = frac1(kappa * c.k0);
+    const double G = g * c.g;
+    const double SB = bs * c.sb;
     if (!isfinite(K2) || !isfinite(G) || !isfinite(K1)) atomicOr(status, (unsigned)ST_NONFINITE);
     RecT r;
     if constexpr (sizeof(RecT) == sizeof(RecF)) {
@@ -309,8 +325,13 @@ __global__ void records1d_kernel(const DevInst *__restrict__ inst, SchedConst sc
     const int64_t nrec = (int64_t)nstage + 1;
     const DevInst p = inst[i];
     const double t0 = *t_dev + t_off;
+    // the block's instance factors, computed once (one FP64 division per block, not per record)
+    __shared__ RecScale s_c;
+    if (threadIdx.x == 0) s_c = rec_scale(p, sc);
+    __syncthreads();
+    const RecScale c = s_c;
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j <= nstage; j += gridDim.y * blockDim.x)
-        record1d<RecT, SPLIT>(p, sc, t0, j, nstage, fge + i * (int64_t)nstage, rec + i * nrec + j, status);
+        record1d<RecT, SPLIT>(p, sc, c, t0, j, nstage, fge + i * (int64_t)nstage, rec + i * nrec + j, status);
 }
 
 // 3D records (symmetric boxes): one per sub-stage, all three axes
