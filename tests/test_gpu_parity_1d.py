@@ -114,6 +114,26 @@ def test_mixed_trap_laws_in_one_batch(precision, tol, flow):
     assert max(O.rel_l2(o, r) for o, r in zip(outs, refs)) <= budget(tol, steps * 0.01)
 
 
+@pytest.mark.parametrize("flow", [1, 2])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_one_law_with_per_instance_parameters(precision, tol, flow):
+    """Instances that share the law kind but not its parameters: the schedule
+    is specialised on the law yet evaluates the trap per instance (no shared
+    node table)."""
+    need_gpu()
+    insts, psis = [], []
+    for k, lawp in enumerate([[0.3, 1.0, 0.0], [0.2, 2.5, 0.4], [0.45, 0.7, -1.0]]):
+        inst = W.Instance(n=[256 << k], a=[-12.0], b=[12.0], omega_law=W.OMEGA_SIN, w0=0.8 + 0.3 * k, law=lawp,
+                          eps=0.05, vi_kind=W.VI_COS, vi_k=1.5, sigma=4.0, ho_flow=flow, h=0.01)
+        x = inst.x()
+        insts.append(inst)
+        psis.append((inst.w0 / math.pi) ** 0.25 * np.exp(-inst.w0 * (x - 0.2) ** 2 / 2).astype(complex))
+    steps = 100
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    outs = _run_gpu(insts, psis, steps, precision, 0.01, flow=flow)
+    assert max(O.rel_l2(o, r) for o, r in zip(outs, refs)) <= budget(tol, steps * 0.01)
+
+
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_mixed_perturbations_and_boxes_in_one_batch(precision, tol):
     """Instances with different perturbation kinds (cos, x^4, none) and a
