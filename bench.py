@@ -391,7 +391,9 @@ def run_native(args):
                      "hbm_equivalent_GBps": hbm_equiv, "hbm_equivalent_frac_of_measured": hbm_equiv / hbm},
         "e2e": {"value": gps_all / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
                 "h2d_bytes_per_step": int(host0.nbytes), "d2h_bytes_per_step": int(host0.nbytes)},
-        "gpu_launches": 4 * args.steps,
+        # per solve (one schedule chunk, resident): law_nodes (the batch shares the trap law),
+        # stage_flow, records, step1d, advance_time
+        "gpu_launches": 5 * args.steps,
         "kernel_ms_per_launch": step_ms,
         "clocks": clk.summary(),
         "status": st,
