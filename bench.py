@@ -402,7 +402,12 @@ def run_native(args):
     if rank == 0 and not args.no_extras:
         line["extras"] = extra_measurements(hfs, W, torch)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        # the e2e solves started from psi0 of this batch: pinned_out holds psi(T)
+        same = COUNT_ == COUNT and STEPS_ == STEPS and rank_seed(rank) == 20100703
+        final = pinned_out.numpy().view(np.complex64) if same else None
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample, final, [i.n[0] for i in insts])
+        if final is not None:
+            line["error"] = line["cpu_baseline"].pop("error")
     if rank == 0:
         print(json.dumps(line))
     solver.close()
@@ -410,7 +415,7 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-def _stratified_sample(per_size: int, seed: int):
+def _stratified_sample(per_size: int, seed: int, with_index: bool = False):
     from paper_1007_3470_gb300 import workloads as W
     insts, psis, _ = W.batch_1d(count=COUNT, seed=seed, h=DT, steps=STEPS)
     pick, seen = [], {}
@@ -419,24 +424,45 @@ def _stratified_sample(per_size: int, seed: int):
         if seen.get(n, 0) < per_size:
             seen[n] = seen.get(n, 0) + 1
             pick.append(i)
-    return [insts[i] for i in pick], [psis[i] for i in pick]
+    out = [insts[i] for i in pick], [psis[i] for i in pick]
+    return (*out, pick) if with_index else out
 
 
-def cpu_baseline(per_size: int):
+def result_error(gpu_state: np.ndarray, sizes, pick, psis0, refs) -> dict:
+    """Relative L2 error of the GPU's psi(T) against the oracle's on the
+    sampled instances (gpu_state: the whole batch, concatenated), and the norm
+    drift dx sum |psi|^2 (T) - (0) of the GPU result."""
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    errs, drift = [], []
+    for i, p0, r in zip(pick, psis0, refs):
+        g = gpu_state[off[i]:off[i + 1]].astype(np.complex128)
+        errs.append(np.linalg.norm(g - r) / np.linalg.norm(r))
+        drift.append(abs(np.sum(np.abs(g) ** 2) - np.sum(np.abs(p0) ** 2)) / np.sum(np.abs(p0) ** 2))
+    T = STEPS * DT
+    return {"rel_l2_max": float(np.max(errs)), "rel_l2_median": float(np.median(errs)),
+            "bound": 1e-5 * max(T, 1.0), "within_bound": bool(np.max(errs) <= 1e-5 * max(T, 1.0)),
+            "norm_drift_max": float(np.max(drift)), "instances": len(errs), "vs": "FP64 oracle"}
+
+
+def cpu_baseline(per_size: int, gpu_state=None, sizes=None):
     """The FP64 oracle, as it stands, on a stratified sample of the workload
     (per_size instances of every grid size, all 500 steps), OpenMP over
-    instances on every host core."""
+    instances on every host core.  With the GPU's final state of the same
+    batch, its results also give the error of that state (result_error)."""
     from oracle import oracle as O
-    insts, psis = _stratified_sample(per_size, 20100703)
+    insts, psis, pick = _stratified_sample(per_size, 20100703, with_index=True)
     probs = [O.Problem(**i.as_dict()) for i in insts]
     cores = O.max_threads()
     t0 = time.perf_counter()
-    O.run_batch(probs, psis, STEPS, cores)
+    refs = O.run_batch(probs, psis, STEPS, cores)
     dt = time.perf_counter() - t0
     gps = sum(i.n[0] for i in insts) * STEPS
-    return {"value": gps / dt, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(insts)} instances ({per_size} per grid size 128..4096) x {STEPS} steps, "
-                      f"FP64 stage-by-stage oracle, {dt:.1f} s"}
+    out = {"value": gps / dt, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(insts)} instances ({per_size} per grid size 128..4096) x {STEPS} steps, "
+                     f"FP64 stage-by-stage oracle, {dt:.1f} s"}
+    if gpu_state is not None:
+        out["error"] = result_error(gpu_state, sizes, pick, psis, refs)
+    return out
 
 
 def run_case(args):

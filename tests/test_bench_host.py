@@ -42,3 +42,21 @@ def test_cpu_baseline_sample_is_stratified():
     sizes = sorted(i.n[0] for i in insts)
     assert sizes == sorted([n for n in (128, 256, 512, 1024, 2048, 4096) for _ in range(2)])
     assert all(len(p) == i.n[0] for i, p in zip(insts, psis))
+
+
+def test_result_error_against_reference_slices():
+    """result_error slices each sampled instance out of the concatenated
+    batch and compares it with its reference."""
+    import numpy as np
+    rng = np.random.default_rng(1)
+    sizes = [4, 8, 4]
+    refs_all = [rng.standard_normal(n) + 1j * rng.standard_normal(n) for n in sizes]
+    state = np.concatenate(refs_all).astype(np.complex64)
+    pick = [0, 2]
+    psis0 = [refs_all[0], refs_all[2]]
+    e = bench.result_error(state, sizes, pick, psis0, [refs_all[0], refs_all[2]])
+    assert e["rel_l2_max"] < 1e-6 and e["instances"] == 2 and e["norm_drift_max"] < 1e-6
+    bad = state.copy()
+    bad[12:16] *= 1.01  # instance 2 scaled by 1 %
+    e = bench.result_error(bad, sizes, pick, psis0, [refs_all[0], refs_all[2]])
+    assert abs(e["rel_l2_max"] - 0.01) < 1e-5 and not e["within_bound"]
