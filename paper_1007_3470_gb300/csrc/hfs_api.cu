@@ -10,12 +10,24 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hfs.h"
 #include "hfs_internal.cuh"
 #include "hfs_sched.h"
 #include "hfs_step3d.h"
 
 using namespace hfs;
+
+namespace {
+// NVTX range around an entry point (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 namespace hfs {
 
@@ -621,6 +633,7 @@ int hfs_get_psi(hfs_ctx_t c, void *dst, int on_device)
 
 int hfs_step(hfs_ctx_t c, int64_t nsteps)
 {
+    NvtxRange nvtx_range("hfs_step");
     int s = ready(c);
     if (s) return s;
     if (!c->have_sched) return HFS_ERR_NOT_READY;
@@ -694,6 +707,7 @@ static int run_diag(hfs_ctx_s *c)
 
 int hfs_norm(hfs_ctx_t c, double *out)
 {
+    NvtxRange nvtx_range("hfs_norm");
     int s = ready(c);
     if (s) return s;
     if (!out) return HFS_ERR_INVALID_ARG;
@@ -705,6 +719,7 @@ int hfs_norm(hfs_ctx_t c, double *out)
 
 int hfs_energy(hfs_ctx_t c, double *out)
 {
+    NvtxRange nvtx_range("hfs_energy");
     int s = ready(c);
     if (s) return s;
     if (!out) return HFS_ERR_INVALID_ARG;
@@ -742,6 +757,7 @@ int hfs_set_plan(hfs_ctx_t c, int n, int ept)
 
 int hfs_autotune(hfs_ctx_t c, int trial_steps, int32_t *best_ept)
 {
+    NvtxRange nvtx_range("hfs_autotune");
     int s = ready(c);
     if (s) return s;
     if (!c->have_sched || c->dim != 1 || trial_steps < 1) return HFS_ERR_INVALID_ARG;
