@@ -29,33 +29,32 @@ __device__ __forceinline__ double frac_turns(double m2, double c, double /*unuse
     return p - rint(p);
 }
 
-// u * exp(-2 pi i turns) * scale (FP32).
-// The quarter turn q = rint(4 turns) is split off exactly (only q mod 4
-// matters), leaving theta = 2 pi (turns - q/4) with |theta| <= pi/4, where sin is the
-// Taylor series to theta^9 and cos - 1 the series to theta^10 (truncation
-// below 2e-9).  The small rotation is applied as u + u (cos - 1 - i sin):
-// rounding cos theta itself to FP32 would return exactly 1 for
-// |theta| < 2.4e-4 while sin theta stays accurate, so |exp(-i theta)|^2 would
-// come out as 1 + theta^2, a norm gain of fixed sign at every step for the
-// low wavenumbers and the trap centre, where most of the norm sits.  The
-// quarter turn (-i)^q is then an exact swap / negation.
-__device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, float scale)
+// sin theta and cos theta - 1 for theta = 2 pi f, |f| <= 1/8 (plus
+// rounding): the Taylor series to theta^9 and theta^10 (truncation below
+// 2e-9).  cos - 1 rather than cos: rounding cos theta itself to FP32 would
+// return exactly 1 for |theta| < 2.4e-4 while sin theta stays accurate, so
+// |exp(-i theta)|^2 would come out as 1 + theta^2, a norm gain of fixed sign
+// at every step for the low wavenumbers and the trap centre, where most of
+// the norm sits.
+__device__ __forceinline__ void small_rotation(float f, float &sn, float &cm1)
 {
-    // rint(4 turns) and turns - q/4 are exact: the same quarter turn mod 4 and
-    // remainder as after a reduction of turns mod 1
-    const float q = rintf(4.0f * turns);
-    const float f = fmaf(q, -0.25f, turns);  // exact
     const float th = f * 6.28318530717958647692f;
     const float t2 = th * th;
     float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
     ps = fmaf(ps, t2, 1.0f / 120.0f);
     ps = fmaf(ps, t2, -1.0f / 6.0f);
-    const float sn = fmaf(th * t2, ps, th);
+    sn = fmaf(th * t2, ps, th);
     float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
     pc = fmaf(pc, t2, -1.0f / 720.0f);
     pc = fmaf(pc, t2, 1.0f / 24.0f);
     pc = fmaf(pc, t2, -0.5f);
-    const float cm1 = t2 * pc;  // cos(theta) - 1
+    cm1 = t2 * pc;
+}
+
+// u (1 + cm1 - i sn), then the exact quarter turn (-i)^q (a swap and
+// negations; only q mod 4 matters) and the scale
+__device__ __forceinline__ cpx<float> finish_rotation(cpx<float> u, float q, float sn, float cm1, float scale)
+{
     const float wx = u.x + fmaf(u.x, cm1, u.y * sn);
     const float wy = u.y + fmaf(u.y, cm1, -u.x * sn);
     const int qi = ((int)q) & 3;
@@ -66,33 +65,57 @@ __device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, flo
     return {ox * scale, oy * scale};
 }
 
-// Two grid points at once: the same per-lane operations as frac_turns /
-// apply_turns above; with PK the FP32 arithmetic runs in packed two-lane
-// instructions (sm_100 family), so the results are bit-identical either way.
+// u * exp(-2 pi i turns) * scale (FP32).  The quarter turn q = rint(4 turns)
+// is split off exactly: rint(4 turns) and turns - q/4 are exact and give the
+// same quarter turn mod 4 and the same remainder as after a reduction of
+// turns mod 1, leaving theta = 2 pi (turns - q/4), |theta| <= pi/4.
+__device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, float scale)
+{
+    const float q = rintf(4.0f * turns);
+    float sn, cm1;
+    small_rotation(fmaf(q, -0.25f, turns), sn, cm1);
+    return finish_rotation(u, q, sn, cm1, scale);
+}
+
+// The merged phases of a pair of grid points, in turns, as an exact part r
+// (the reduced product hi m2 - rint(hi m2), |r| <= 1/2) plus a correction c
+// (the product's rounding error, lo m2 and any further terms).  The angle is
+// rounded once, after the quarter turn is split off: (r - q/4) is exact and
+// |r - q/4 + c| <= 1/8, so the rounding is 4x finer than that of the sum
+// r + c at magnitude up to 1/2 (the error of the FP32 path is set by phase
+// and state rounding accumulated over the steps).
+struct Turns2 {
+    float2 r, c;
+};
+
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 rint2(float2 a) { return make_float2(rintf(a.x), rintf(a.y)); }
 __device__ __forceinline__ float2 bc2(float c) { return make_float2(c, c); }
 
-template <bool PK> __device__ __forceinline__ float2 frac_turns2(float2 m2, float hi, float lo)
+// With PK the FP32 arithmetic runs in packed two-lane instructions (sm_100
+// family) on both points at once, otherwise lane by lane; the per-lane
+// operations are the same, so the results are bit-identical either way.
+template <bool PK> __device__ __forceinline__ float2 add2(float2 a, float2 b)
 {
-    if constexpr (PK) {
-        const float2 p = __fmul2_rn(bc2(hi), m2);
-        const float2 err = __ffma2_rn(bc2(hi), m2, neg2(p));
-        const float2 r = __fadd2_rn(p, neg2(rint2(p)));
-        return __fadd2_rn(r, __ffma2_rn(bc2(lo), m2, err));
-    } else {
-        return make_float2(frac_turns(m2.x, hi, lo), frac_turns(m2.y, hi, lo));
-    }
+    if constexpr (PK) return __fadd2_rn(a, b);
+    else return make_float2(a.x + b.x, a.y + b.y);
 }
 
-// the small-rotation part of apply_turns for two points: quarter turns q,
-// sin theta and cos theta - 1
-// (no separate reduction mod 1: rint(4 turns) and turns - q/4 are exact and
-// give the same quarter turn mod 4 and the same remainder as after one)
-__device__ __forceinline__ void small_rotation2(float2 turns, float2 &q, float2 &sn, float2 &cm1)
+template <bool PK> __device__ __forceinline__ float2 mul2(float2 a, float2 b)
 {
-    q = rint2(__fmul2_rn(bc2(4.0f), turns));
-    const float2 f = __ffma2_rn(q, bc2(-0.25f), turns);
+    if constexpr (PK) return __fmul2_rn(a, b);
+    else return make_float2(a.x * b.x, a.y * b.y);
+}
+
+template <bool PK> __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    if constexpr (PK) return __ffma2_rn(a, b, c);
+    else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+
+// small_rotation for two angles in packed FP32
+__device__ __forceinline__ void small_rotation2(float2 f, float2 &sn, float2 &cm1)
+{
     const float2 th = __fmul2_rn(f, bc2(6.28318530717958647692f));
     const float2 t2 = __fmul2_rn(th, th);
     float2 ps = __ffma2_rn(t2, bc2(1.0f / 362880.0f), bc2(-1.0f / 5040.0f));
@@ -106,31 +129,48 @@ __device__ __forceinline__ void small_rotation2(float2 turns, float2 &q, float2 
     cm1 = __fmul2_rn(t2, pc);
 }
 
-// u (1 + cm1 - i sn) followed by the exact quarter turn (-i)^q and the scale
-__device__ __forceinline__ cpx<float> finish_rotation(cpx<float> u, float q, float sn, float cm1, float scale)
+// (hi + lo) m2 mod 1 for two exact float integers m2 (< 2^23)
+template <bool PK> __device__ __forceinline__ Turns2 frac_turns2(float2 m2, float hi, float lo)
 {
-    const float wx = u.x + fmaf(u.x, cm1, u.y * sn);
-    const float wy = u.y + fmaf(u.y, cm1, -u.x * sn);
-    const int qi = ((int)q) & 3;
-    float ox = (qi & 1) ? wy : wx;
-    float oy = (qi & 1) ? wx : wy;
-    ox = (qi >= 2) ? -ox : ox;
-    oy = (qi == 1 || qi == 2) ? -oy : oy;
-    return {ox * scale, oy * scale};
+    if constexpr (PK) {
+        const float2 p = __fmul2_rn(bc2(hi), m2);
+        const float2 err = __ffma2_rn(bc2(hi), m2, neg2(p));  // exact rounding error of the product
+        return {__fadd2_rn(p, neg2(rint2(p))), __ffma2_rn(bc2(lo), m2, err)};
+    } else {
+        Turns2 t;
+        const float px = hi * m2.x, py = hi * m2.y;
+        t.r = make_float2(px - rintf(px), py - rintf(py));
+        t.c = make_float2(fmaf(lo, m2.x, fmaf(hi, m2.x, -px)), fmaf(lo, m2.y, fmaf(hi, m2.y, -py)));
+        return t;
+    }
 }
 
 template <bool PK>
+__device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Turns2 t, float scale)
+{
+    const float2 q = rint2(mul2<PK>(bc2(4.0f), add2<PK>(t.r, t.c)));
+    const float2 f = add2<PK>(fma2<PK>(q, bc2(-0.25f), t.r), t.c);
+    float2 sn, cm1;
+    if constexpr (PK) {
+        small_rotation2(f, sn, cm1);
+    } else {
+        small_rotation(f.x, sn.x, cm1.x);
+        small_rotation(f.y, sn.y, cm1.y);
+    }
+    u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
+    u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
+}
+
+// One-part form in packed FP32: the phase summed first, then the quarter turn
+// split off as in apply_turns (the 3D plane kernels, where keeping the two
+// parts live costs register spills)
 __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, float2 turns, float scale)
 {
-    if constexpr (PK) {
-        float2 q, sn, cm1;
-        small_rotation2(turns, q, sn, cm1);
-        u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
-        u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
-    } else {
-        u0 = apply_turns(u0, turns.x, scale);
-        u1 = apply_turns(u1, turns.y, scale);
-    }
+    const float2 q = rint2(__fmul2_rn(bc2(4.0f), turns));
+    float2 sn, cm1;
+    small_rotation2(__ffma2_rn(q, bc2(-0.25f), turns), sn, cm1);
+    u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
+    u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
 }
 
 __device__ __forceinline__ cpx<double> apply_turns(cpx<double> u, double turns, double scale)

@@ -103,15 +103,15 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
         if (e % PHASE_GROUP == 0) fence_group(v, e);
         const int m0 = t + T * e - N / 2, m1 = m0 + T;
         const float2 mf = make_float2((float)m0, (float)m1);
-        float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.k2hi, rc.k2lo);
+        Turns2 tt = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.k2hi, rc.k2lo);
         if (VI < 0 && tp.asym) {
-            const float2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
-            turns = make_float2(turns.x + (lin.x + rc.k0), turns.y + (lin.y + rc.k0));
+            // the linear chirp term of an off-centre box, into the correction
+            const Turns2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
+            tt.c = add2<PK>(tt.c, add2<PK>(add2<PK>(lin.r, lin.c), bc2(rc.k0)));
         }
         const float2 F = make_float2(xphase_F<VI>(v[e], mf.x, tp), xphase_F<VI>(v[e + 1], mf.y, tp));
-        if constexpr (PK) turns = __ffma2_rn(bc2(rc.sb2pi), F, turns);
-        else turns = make_float2(fmaf(rc.sb2pi, F.x, turns.x), fmaf(rc.sb2pi, F.y, turns.y));
-        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f);
+        tt.c = fma2<PK>(bc2(rc.sb2pi), F, tt.c);
+        apply_turns2<PK>(v[e], v[e + 1], tt, 1.0f);
     }
 }
 
@@ -144,8 +144,8 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E
         const int k0 = t + T * e, k1 = k0 + T;
         const int m0 = (k0 < N / 2) ? k0 : k0 - N;
         const int m1 = (k1 < N / 2) ? k1 : k1 - N;
-        const float2 turns = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.ghi, rc.glo);
-        apply_turns2<PK>(v[e], v[e + 1], turns, 1.0f / N);
+        apply_turns2<PK>(v[e], v[e + 1], frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.ghi, rc.glo),
+                         1.0f / N);
     }
 }
 

@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(c
             for (int e = 0; e < E; e += 2) {
                 const int kz0 = t + T * e, kz1 = kz0 + T;
                 const int mz0 = (kz0 < N / 2) ? kz0 : kz0 - N, mz1 = (kz1 < N / 2) ? kz1 : kz1 - N;
-                const float2 tz = frac_turns2<true>(make_float2((float)(mz0 * mz0), (float)(mz1 * mz1)), rc.g[2],
+                const Turns2 tz = frac_turns2<true>(make_float2((float)(mz0 * mz0), (float)(mz1 * mz1)), rc.g[2],
                                                     rc.glo[2]);
-                apply_turns2<true>(v[e], v[e + 1], __fadd2_rn(bc2(txy), tz), scale);
+                apply_turns2(v[e], v[e + 1], __fadd2_rn(bc2(txy), __fadd2_rn(tz.r, tz.c)), scale);
             }
         } else {
 #pragma unroll
@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
 #pragma unroll
                 for (int e = 0; e < E; e += 2) {
                     const int mx0 = t + T * e - N / 2, mx1 = mx0 + T;
-                    float2 turns = frac_turns2<true>(make_float2((float)(mx0 * mx0), (float)(mx1 * mx1)), rc.k2[0],
-                                                     rc.k2lo[0]);
-                    turns = __fadd2_rn(turns, bc2(tyz));
+                    const Turns2 tx = frac_turns2<true>(make_float2((float)(mx0 * mx0), (float)(mx1 * mx1)), rc.k2[0],
+                                                        rc.k2lo[0]);
+                    float2 turns = __fadd2_rn(__fadd2_rn(tx.r, tx.c), bc2(tyz));
                     turns = __ffma2_rn(bc2(rc.sb2pi), make_float2(Fof(v[e], mx0), Fof(v[e + 1], mx1)), turns);
-                    apply_turns2<true>(v[e], v[e + 1], turns, 1.0f);
+                    apply_turns2(v[e], v[e + 1], turns, 1.0f);
                 }
             }
             if constexpr (MODE & P_FWD_X) FftPlan<N, E>::template run<false, float>(v, row, t, tw);
