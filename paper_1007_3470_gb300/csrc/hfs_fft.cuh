@@ -236,10 +236,26 @@ template <int ILV> __host__ __device__ constexpr int soff(int c)
     else return c * ILV;
 }
 
+// Barrier around a shared-memory exchange.  TEAM = false: the whole CTA.
+// TEAM = true: only the T threads of the team that owns the buffer (named
+// barrier `bar`, or the warp when a team fits in one), so the teams of a CTA
+// holding several short transforms do not wait for one another.
+template <int T, bool TEAM> __device__ __forceinline__ void exchange_sync(int bar)
+{
+    if constexpr (!TEAM || T >= kCtaThreads) {
+        __syncthreads();
+    } else if constexpr (T <= 32) {
+        __syncwarp();
+    } else {
+        static_assert(T % 32 == 0, "a named barrier counts whole warps");
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(T) : "memory");
+    }
+}
+
 // One Stockham pass; see the layout contract at the top of the file.
-template <int N, int E, int RAD, int NS, bool INV, bool LAST, int ILV, typename R>
+template <int N, int E, int RAD, int NS, bool INV, bool LAST, int ILV, bool TEAM, typename R>
 __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
-                                              const typename TwOf<R>::type *__restrict__ tw)
+                                              const typename TwOf<R>::type *__restrict__ tw, int bar)
 {
     constexpr int T = N / E;
     constexpr int Q = E / RAD;
@@ -279,31 +295,31 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
         }
     }
     if constexpr (!LAST) {
-        __syncthreads();
+        exchange_sync<T, TEAM>(bar);
         const cpx<R> *rd = sm + sbase<ILV>(t);
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = rd[soff<ILV>(T * e)];
-        __syncthreads();
+        exchange_sync<T, TEAM>(bar);
     }
 }
 
-template <int N, int E, bool INV, int ILV, typename R, int NS, int RAD, int... REST>
+template <int N, int E, bool INV, int ILV, bool TEAM, typename R, int NS, int RAD, int... REST>
 __device__ __forceinline__ void fft_passes(cpx<R> (&v)[E], cpx<R> *sm, int t,
-                                           const typename TwOf<R>::type *__restrict__ tw)
+                                           const typename TwOf<R>::type *__restrict__ tw, int bar)
 {
-    stockham_pass<N, E, RAD, NS, INV, sizeof...(REST) == 0, ILV>(v, sm, t, tw);
-    if constexpr (sizeof...(REST) > 0) fft_passes<N, E, INV, ILV, R, NS * RAD, REST...>(v, sm, t, tw);
+    stockham_pass<N, E, RAD, NS, INV, sizeof...(REST) == 0, ILV, TEAM>(v, sm, t, tw, bar);
+    if constexpr (sizeof...(REST) > 0) fft_passes<N, E, INV, ILV, TEAM, R, NS * RAD, REST...>(v, sm, t, tw, bar);
 }
 
 // Radix sequences per (N, elements per thread).
 template <int N, int E> struct FftPlan;
 #define HFS_PLAN(NN, EE, ...)                                                                          \
     template <> struct FftPlan<NN, EE> {                                                                \
-        template <bool INV, typename R, int ILV = 1>                                                    \
+        template <bool INV, typename R, int ILV = 1, bool TEAM = false>                                 \
         static __device__ __forceinline__ void run(cpx<R> (&v)[EE], cpx<R> *sm, int t,                   \
-                                                   const typename TwOf<R>::type *tw)                    \
+                                                   const typename TwOf<R>::type *tw, int bar = 0)       \
         {                                                                                               \
-            fft_passes<NN, EE, INV, ILV, R, 1, __VA_ARGS__>(v, sm, t, tw);                              \
+            fft_passes<NN, EE, INV, ILV, TEAM, R, 1, __VA_ARGS__>(v, sm, t, tw, bar);                   \
         }                                                                                               \
     };
 HFS_PLAN(4096, 16, 16, 16, 16)

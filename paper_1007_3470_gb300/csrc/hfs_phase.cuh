@@ -51,30 +51,42 @@ __device__ __forceinline__ void small_rotation(float f, float &sn, float &cm1)
     cm1 = t2 * pc;
 }
 
-// u (1 + cm1 - i sn), then the exact quarter turn (-i)^q (a swap and
-// negations; only q mod 4 matters) and the scale
-__device__ __forceinline__ cpx<float> finish_rotation(cpx<float> u, float q, float sn, float cm1, float scale)
+// 1.5 * 2^23: for |x| < 2^22, x + kRoundMagic is rounded to an integer (to
+// nearest, ties to even, as rint) held in the low mantissa bits, so one
+// addition gives rint(x) (the sum minus kRoundMagic, exact) and rint(x) mod 4
+// (the low two bits of the sum's encoding: 2^22 + rint(x) = rint(x) mod 4).
+// x = 4 turns here; an FP32 phase of 2^20 turns or more has lost its angle
+// to rounding (ulp >= 1/8 turn) in any form.
+constexpr float kRoundMagic = 12582912.0f;
+
+// u (1 + cm1 - i sn) scale, then the exact quarter turn (-i)^qi (a swap and
+// sign flips).  The power-of-two scale is folded in: the caller passes
+// sn scale and cm1 scale (exact), and u scale + u (cm1 - i sn) scale rounds
+// exactly as (u + u (cm1 - i sn)) scale would.
+__device__ __forceinline__ cpx<float> finish_rotation(cpx<float> u, int qi, float sn, float cm1, float scale)
 {
-    const float wx = u.x + fmaf(u.x, cm1, u.y * sn);
-    const float wy = u.y + fmaf(u.y, cm1, -u.x * sn);
-    const int qi = ((int)q) & 3;
-    float ox = (qi & 1) ? wy : wx;
-    float oy = (qi & 1) ? wx : wy;
-    ox = (qi >= 2) ? -ox : ox;
-    oy = (qi == 1 || qi == 2) ? -oy : oy;
-    return {ox * scale, oy * scale};
+    const float wx = fmaf(u.x, scale, fmaf(u.x, cm1, u.y * sn));
+    const float wy = fmaf(u.y, scale, fmaf(u.y, cm1, -u.x * sn));
+    const bool swap = qi & 1;
+    const float ox = swap ? wy : wx;
+    const float oy = swap ? wx : wy;
+    const unsigned nx = (unsigned)(qi & 2) << 30;                // -x for qi = 2, 3
+    const unsigned ny = (unsigned)((qi ^ (qi << 1)) & 2) << 30;  // -y for qi = 1, 2
+    return {__int_as_float(__float_as_int(ox) ^ nx), __int_as_float(__float_as_int(oy) ^ ny)};
 }
 
-// u * exp(-2 pi i turns) * scale (FP32).  The quarter turn q = rint(4 turns)
-// is split off exactly: rint(4 turns) and turns - q/4 are exact and give the
-// same quarter turn mod 4 and the same remainder as after a reduction of
-// turns mod 1, leaving theta = 2 pi (turns - q/4), |theta| <= pi/4.
+// u * exp(-2 pi i turns) * scale (FP32, scale a power of two).  The quarter
+// turn q = rint(4 turns) is split off exactly: rint(4 turns) and
+// turns - q/4 are exact and give the same quarter turn mod 4 and the same
+// remainder as after a reduction of turns mod 1, leaving
+// theta = 2 pi (turns - q/4), |theta| <= pi/4.
 __device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, float scale)
 {
-    const float q = rintf(4.0f * turns);
+    const float tq = fmaf(4.0f, turns, kRoundMagic);
+    const float q = tq - kRoundMagic;
     float sn, cm1;
     small_rotation(fmaf(q, -0.25f, turns), sn, cm1);
-    return finish_rotation(u, q, sn, cm1, scale);
+    return finish_rotation(u, __float_as_int(tq) & 3, sn * scale, cm1 * scale, scale);
 }
 
 // The merged phases of a pair of grid points, in turns, as an exact part r
@@ -148,7 +160,8 @@ template <bool PK> __device__ __forceinline__ Turns2 frac_turns2(float2 m2, floa
 template <bool PK>
 __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Turns2 t, float scale)
 {
-    const float2 q = rint2(mul2<PK>(bc2(4.0f), add2<PK>(t.r, t.c)));
+    const float2 tq = fma2<PK>(bc2(4.0f), add2<PK>(t.r, t.c), bc2(kRoundMagic));
+    const float2 q = add2<PK>(tq, bc2(-kRoundMagic));
     const float2 f = add2<PK>(fma2<PK>(q, bc2(-0.25f), t.r), t.c);
     float2 sn, cm1;
     if constexpr (PK) {
@@ -157,8 +170,10 @@ __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Tur
         small_rotation(f.x, sn.x, cm1.x);
         small_rotation(f.y, sn.y, cm1.y);
     }
-    u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
-    u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
+    sn = mul2<PK>(sn, bc2(scale));
+    cm1 = mul2<PK>(cm1, bc2(scale));
+    u0 = finish_rotation(u0, __float_as_int(tq.x) & 3, sn.x, cm1.x, scale);
+    u1 = finish_rotation(u1, __float_as_int(tq.y) & 3, sn.y, cm1.y, scale);
 }
 
 // One-part form in packed FP32: the phase summed first, then the quarter turn
@@ -166,11 +181,14 @@ __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Tur
 // parts live costs register spills)
 __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, float2 turns, float scale)
 {
-    const float2 q = rint2(__fmul2_rn(bc2(4.0f), turns));
+    const float2 tq = __ffma2_rn(bc2(4.0f), turns, bc2(kRoundMagic));
+    const float2 q = __fadd2_rn(tq, bc2(-kRoundMagic));
     float2 sn, cm1;
     small_rotation2(__ffma2_rn(q, bc2(-0.25f), turns), sn, cm1);
-    u0 = finish_rotation(u0, q.x, sn.x, cm1.x, scale);
-    u1 = finish_rotation(u1, q.y, sn.y, cm1.y, scale);
+    sn = __fmul2_rn(sn, bc2(scale));
+    cm1 = __fmul2_rn(cm1, bc2(scale));
+    u0 = finish_rotation(u0, __float_as_int(tq.x) & 3, sn.x, cm1.x, scale);
+    u1 = finish_rotation(u1, __float_as_int(tq.y) & 3, sn.y, cm1.y, scale);
 }
 
 __device__ __forceinline__ cpx<double> apply_turns(cpx<double> u, double turns, double scale)

@@ -58,6 +58,10 @@ constexpr int PHASE_GROUP = HFS_PHASE_GROUP;
 // Phase arithmetic of point pairs in packed FP32 instructions for plans with
 // at least this many values per thread (all plans; measured 2-5 % faster
 // than the scalar form for both 8 and 16 values per thread).
+// FFT exchanges synchronise each instance's team alone (named barrier 1 + g)
+#ifndef HFS_TEAM_SYNC
+#define HFS_TEAM_SYNC true
+#endif
 #ifndef HFS_PACK_PHASE_MIN_E
 #define HFS_PACK_PHASE_MIN_E 8
 #endif
@@ -77,13 +81,12 @@ template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E]
 // merged x-phase X_j on the register layout (position t + T e)
 // the phase argument of one point (turns) before the B-flow term
 template <int VI>
-__device__ __forceinline__ float xphase_F(cpx<float> u, float mf, const TeamParams<float> &tp)
+__device__ __forceinline__ float xphase_F(cpx<float> u, float x, const TeamParams<float> &tp)
 {
     const float dens = u.x * u.x + u.y * u.y;
     if constexpr (VI == HFS_VI_NONE) {
         return tp.sigma * dens;
     } else {
-        const float x = VI < 0 ? fmaf(mf, tp.dx, tp.xc) : mf * tp.dx;
         return fmaf(tp.sigma, dens, tp.eps * vi_eval(VI < 0 ? tp.vikind : VI, x, tp.vik));
     }
 }
@@ -98,18 +101,25 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
     constexpr int T = N / E;
     constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
     static_assert(E % 2 == 0 && PHASE_GROUP % 2 == 0, "points are phased in pairs");
+    // grid index m = t + T e - N/2 and m^2 in FP32 (exact: |m| <= 2048)
+    float tb = (float)(t - N / 2);
 #pragma unroll
     for (int e = 0; e < E; e += 2) {
-        if (e % PHASE_GROUP == 0) fence_group(v, e);
-        const int m0 = t + T * e - N / 2, m1 = m0 + T;
-        const float2 mf = make_float2((float)m0, (float)m1);
-        Turns2 tt = frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.k2hi, rc.k2lo);
+        if (e % PHASE_GROUP == 0) {
+            fence_group(v, e);
+            asm volatile("" : "+f"(tb));
+        }
+        const float2 mf = make_float2(tb + (float)(T * e), tb + (float)(T * (e + 1)));
+        Turns2 tt = frac_turns2<PK>(mul2<PK>(mf, mf), rc.k2hi, rc.k2lo);
         if (VI < 0 && tp.asym) {
             // the linear chirp term of an off-centre box, into the correction
             const Turns2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
             tt.c = add2<PK>(tt.c, add2<PK>(add2<PK>(lin.r, lin.c), bc2(rc.k0)));
         }
-        const float2 F = make_float2(xphase_F<VI>(v[e], mf.x, tp), xphase_F<VI>(v[e + 1], mf.y, tp));
+        float2 x = mf;
+        if constexpr (VI != HFS_VI_NONE)
+            x = VI < 0 ? fma2<PK>(mf, bc2(tp.dx), bc2(tp.xc)) : mul2<PK>(mf, bc2(tp.dx));
+        const float2 F = make_float2(xphase_F<VI>(v[e], x.x, tp), xphase_F<VI>(v[e + 1], x.y, tp));
         tt.c = fma2<PK>(bc2(rc.sb2pi), F, tt.c);
         apply_turns2<PK>(v[e], v[e + 1], tt, 1.0f);
     }
@@ -138,14 +148,18 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E
 {
     constexpr int T = N / E;
     constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
+    // wavenumber index of k = t + T e: k for k < N/2, k - N above; with
+    // 0 <= t < T that is e < E/2, known at compile time.  In FP32, exact.
+    float tf = (float)t;
 #pragma unroll
     for (int e = 0; e < E; e += 2) {
-        if (e % PHASE_GROUP == 0) fence_group(v, e);
-        const int k0 = t + T * e, k1 = k0 + T;
-        const int m0 = (k0 < N / 2) ? k0 : k0 - N;
-        const int m1 = (k1 < N / 2) ? k1 : k1 - N;
-        apply_turns2<PK>(v[e], v[e + 1], frac_turns2<PK>(make_float2((float)(m0 * m0), (float)(m1 * m1)), rc.ghi, rc.glo),
-                         1.0f / N);
+        if (e % PHASE_GROUP == 0) {
+            fence_group(v, e);
+            asm volatile("" : "+f"(tf));
+        }
+        const float2 mf = make_float2(tf + (float)(T * e - (2 * e < E ? 0 : N)),
+                                      tf + (float)(T * (e + 1) - (2 * (e + 1) < E ? 0 : N)));
+        apply_turns2<PK>(v[e], v[e + 1], frac_turns2<PK>(mul2<PK>(mf, mf), rc.ghi, rc.glo), 1.0f / N);
     }
 }
 
@@ -192,9 +206,9 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         asm volatile("" : "+r"(tl));
 #endif
         xphase<N, E, VI>(v, tl, rc, tp);
-        FftPlan<N, E>::template run<false, R>(v, sm, tl, tw);
+        FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
         kphase<N, E>(v, tl, rc);
-        FftPlan<N, E>::template run<true, R>(v, sm, tl, tw);
+        FftPlan<N, E>::template run<true, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
     }
     if (a.final_x) {
         const Rec rc = rec[a.j1];
