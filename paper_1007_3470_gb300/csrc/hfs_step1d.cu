@@ -116,7 +116,8 @@ __global__ void twiddle_kernel(float4 *tf, double2 *td)
 // ---------------------------------------------------------------------------
 size_t step1d_smem_bytes(bool fp64)
 {
-    return (size_t)(kCtaThreads / (4096 / 16)) * smem_elems(4096) * (fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>));
+    if (fp64) return (size_t)step1d_exchange_elems * sizeof(cpx<double>);
+    return (size_t)step1d_exchange_elems * sizeof(cpx<float>) + (size_t)step1d_vtable_floats * sizeof(float);
 }
 
 static cudaError_t prepare_diag(bool fp64)

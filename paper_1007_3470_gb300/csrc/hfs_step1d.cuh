@@ -79,24 +79,23 @@ template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E]
 }
 
 // merged x-phase X_j on the register layout (position t + T e)
-// the phase argument of one point (turns) before the B-flow term
-template <int VI>
-__device__ __forceinline__ float xphase_F(cpx<float> u, float x, const TeamParams<float> &tp)
+// eps V_I(x) at a thread's own grid points (VI = -1: the instance's kind,
+// zero when eps = 0; VI >= 0: the launch's kind on a box symmetric about 0)
+template <int VI> __device__ __forceinline__ float eps_vi(float mf, const TeamParams<float> &tp)
 {
-    const float dens = u.x * u.x + u.y * u.y;
-    if constexpr (VI == HFS_VI_NONE) {
-        return tp.sigma * dens;
-    } else {
-        return fmaf(tp.sigma, dens, tp.eps * vi_eval(VI < 0 ? tp.vikind : VI, x, tp.vik));
-    }
+    const float x = VI < 0 ? fmaf(mf, tp.dx, tp.xc) : mf * tp.dx;
+    return tp.eps * vi_eval(VI < 0 ? tp.vikind : VI, x, tp.vik);
 }
 
 // VI >= 0: every instance of the launch has the perturbation kind VI and a
 // box symmetric about 0 (compile-time, no per-point tests); VI = -1: both
 // read from the team's instance.  Run-time tests inside the unrolled loop
 // were evaluated for every point, both branches (7 % of the kernel time).
+// vt: eps V_I at positions t + T e, written once per work item by the same
+// thread (V_I does not depend on time), so no step re-evaluates it.
 template <int N, int E, int VI>
-__device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp)
+__device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp,
+                                       const float *vt)
 {
     constexpr int T = N / E;
     constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
@@ -116,17 +115,20 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
             const Turns2 lin = frac_turns2<PK>(mf, rc.k1hi, rc.k1lo);
             tt.c = add2<PK>(tt.c, add2<PK>(add2<PK>(lin.r, lin.c), bc2(rc.k0)));
         }
-        float2 x = mf;
-        if constexpr (VI != HFS_VI_NONE)
-            x = VI < 0 ? fma2<PK>(mf, bc2(tp.dx), bc2(tp.xc)) : mul2<PK>(mf, bc2(tp.dx));
-        const float2 F = make_float2(xphase_F<VI>(v[e], x.x, tp), xphase_F<VI>(v[e + 1], x.y, tp));
+        // F = sigma |u|^2 + eps V_I(x)
+        const float d0 = v[e].x * v[e].x + v[e].y * v[e].y;
+        const float d1 = v[e + 1].x * v[e + 1].x + v[e + 1].y * v[e + 1].y;
+        float2 F;
+        if constexpr (VI == HFS_VI_NONE) F = mul2<PK>(bc2(tp.sigma), make_float2(d0, d1));
+        else F = fma2<PK>(bc2(tp.sigma), make_float2(d0, d1), make_float2(vt[t + T * e], vt[t + T * (e + 1)]));
         tt.c = fma2<PK>(bc2(rc.sb2pi), F, tt.c);
         apply_turns2<PK>(v[e], v[e + 1], tt, 1.0f);
     }
 }
 
 template <int N, int E, int VI>
-__device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &rc, const TeamParams<double> &tp)
+__device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &rc, const TeamParams<double> &tp,
+                                       const float *)
 {
     constexpr int T = N / E;
 #pragma unroll
@@ -175,6 +177,11 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<double> (&v)[
     }
 }
 
+// complex elements of the exchange buffers of a CTA (the largest over the
+// plans: E = 16 values per thread), and floats of the eps V_I table after them
+constexpr int step1d_exchange_elems = (kCtaThreads / (4096 / 16)) * smem_elems(4096);
+constexpr int step1d_vtable_floats = kCtaThreads * 16;
+
 template <typename R, int VI, int N, int E>
 __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
 {
@@ -194,6 +201,13 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = active ? psi[t + T * e] : cpx<R>{R(0), R(0)};
+    // FP32: the table of eps V_I behind the exchange buffers (each thread
+    // reads back only the entries it wrote)
+    float *vt = reinterpret_cast<float *>(smem + step1d_exchange_elems) + g * N;
+    if constexpr (sizeof(R) == 4 && VI != HFS_VI_NONE) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) vt[t + T * e] = eps_vi<VI>((float)(t + T * e - N / 2), tp);
+    }
 
     for (int64_t j = a.j0; j < a.j1; ++j) {
         const Rec rc = rec[j];
@@ -205,14 +219,14 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 #ifndef HFS_NO_STEP_LAUNDER
         asm volatile("" : "+r"(tl));
 #endif
-        xphase<N, E, VI>(v, tl, rc, tp);
+        xphase<N, E, VI>(v, tl, rc, tp, vt);
         FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
         kphase<N, E>(v, tl, rc);
         FftPlan<N, E>::template run<true, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
     }
     if (a.final_x) {
         const Rec rc = rec[a.j1];
-        xphase<N, E, VI>(v, t, rc, tp);
+        xphase<N, E, VI>(v, t, rc, tp, vt);
     }
     if (active) {
         bool bad = false;
