@@ -267,9 +267,7 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
     asm volatile("" : "+l"(twp));
     // likewise the forward and inverse transforms compute identical integer
     // offsets; recomputing them per pass is cheaper than holding them live
-#ifndef HFS_NO_PASS_LAUNDER
     asm volatile("" : "+r"(t));
-#endif
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         cpx<R> a[RAD];

@@ -55,22 +55,20 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
 #define HFS_PHASE_GROUP 4
 #endif
 constexpr int PHASE_GROUP = HFS_PHASE_GROUP;
-// Phase arithmetic of point pairs in packed FP32 instructions for plans with
-// at least this many values per thread (all plans; measured 2-5 % faster
-// than the scalar form for both 8 and 16 values per thread).
 // FFT exchanges synchronise each instance's team alone (named barrier 1 + g)
 #ifndef HFS_TEAM_SYNC
 #define HFS_TEAM_SYNC true
 #endif
+// Phase arithmetic of point pairs in packed FP32 instructions for plans with
+// at least this many values per thread (all plans; measured 2-5 % faster
+// than the scalar form for both 8 and 16 values per thread).
 #ifndef HFS_PACK_PHASE_MIN_E
 #define HFS_PACK_PHASE_MIN_E 8
 #endif
 template <int E> __device__ __forceinline__ void fence_group(cpx<float> (&v)[E], int e0)
 {
-#ifndef HFS_NO_PHASE_FENCE
 #pragma unroll
     for (int e = e0; e < e0 + PHASE_GROUP && e < E; ++e) asm volatile("" : "+f"(v[e].x), "+f"(v[e].y));
-#endif
 }
 template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E], int e0)
 {
@@ -216,9 +214,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         // integer and SFU operations) instead of holding 3E of them live
         // across the whole time loop.
         int tl = t;
-#ifndef HFS_NO_STEP_LAUNDER
         asm volatile("" : "+r"(tl));
-#endif
         xphase<N, E, VI>(v, tl, rc, tp, vt);
         FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
         kphase<N, E>(v, tl, rc);
@@ -239,13 +235,9 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     }
 }
 
-#ifdef HFS_ONLY_EPT8
-#define HFS_FOR_EACH_PLAN(X) X(2048, 8) X(1024, 8) X(512, 8) X(256, 8) X(128, 8)
-#else
 #define HFS_FOR_EACH_PLAN(X)                                                                                      \
     X(4096, 16) X(2048, 16) X(1024, 16) X(512, 16) X(256, 16) X(128, 16) X(2048, 8) X(1024, 8) X(512, 8)        \
         X(256, 8) X(128, 8)
-#endif
 
 // FP32: two CTAs per SM (128 registers); FP64 parity mode: one
 #ifndef HFS_STEP1D_MIN_CTAS
