@@ -48,7 +48,7 @@ COUNT, STEPS, DT = 4096, 500, 0.005
 # profiles/), valid only while the kernel's sources hash to "src".
 STEP1D_TRAFFIC = {"src": "4ea1a17fdae44b95",
                   "batch_1d_4096x500_c64": 110536192 + 49964544,
-                  "batch_1d_65536x1_streaming": (733435136 + 895259648 + 733575168 + 892230656) // 2}
+                  "batch_1d_65536x1_streaming": (733567744 + 890993152 + 733393408 + 886624512) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cuh", "hfs_step1d.cu", "hfs_step1d_vicos.cu", "hfs_step1d_vix4.cu", "hfs_step1d_vinone.cu",
                   "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_sched.h")
 
@@ -209,6 +209,7 @@ def extra_measurements(hfs, W, torch):
     ss = hfs.Solver(insts, precision="c64", chunk_steps=STEPS)
     ss.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     ss.set_mode(hfs.HFS_MODE_STREAMING, 1)
+    ss.autotune(trial_steps=2)
     ss.set_graphs(True)
     ss.set_psi(psis)
     ms = kernel_ms(ss, STEPS)
@@ -245,6 +246,8 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
     s = hfs.Solver(insts, precision="c64", chunk_steps=steps)
     s.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     s.set_mode(hfs.HFS_MODE_STREAMING, 1)
+    # plans per grid size measured in this mode (2 trial steps: 44 step launches)
+    tuned = s.autotune(trial_steps=2)
     s.set_graphs(True)
     hfs.hfs_set_profiling(s.h, True)
     s.set_psi(psis)
@@ -262,7 +265,8 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
     return {"instances": count, "points": pts, "state_MB": pts * 8 / 1e6, "time_steps": steps,
             "ms_per_launch": best / steps, "grid_point_steps_per_s": pts * steps / (best * 1e-3),
             "hbm_GBps_algorithmic": gbps, "hbm_frac_of_measured": gbps / hbm,
-            "algorithmic_bytes_per_launch": pts * 16, "dram_bytes_per_launch": traffic, "status": st}
+            "algorithmic_bytes_per_launch": pts * 16, "dram_bytes_per_launch": traffic, "plans_ept": tuned,
+            "status": st}
 
 
 def surrogate_measurement():
