@@ -184,6 +184,20 @@ def test_batched_mixed_sizes(precision, tol):
     assert sorted({i.n[0] for i in insts}) == [128, 256, 512, 1024, 2048, 4096]
 
 
+def test_streaming_many_items_per_cta():
+    """With far more work items than CTAs (every CTA takes several items per
+    launch, every plan size present), streaming launches of one and two
+    steps give bitwise the resident result."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=3000, seed=9)
+    steps = 3
+    base = _run_gpu(insts, psis, steps, "c64", 0.005)
+    for mode in ((hfs.HFS_MODE_STREAMING, 1), (hfs.HFS_MODE_STREAMING, 2)):
+        out = _run_gpu(insts, psis, steps, "c64", 0.005, mode=mode)
+        assert all(np.array_equal(a, b) for a, b in zip(base, out))
+
+
 def test_modes_graphs_and_plans_agree():
     """Streaming (one step per launch), resident, graph replay and both plan
     variants give the same FP32 result (bitwise for the launch modes)."""
