@@ -202,7 +202,8 @@ def extra_measurements(hfs, W, torch):
     ms = kernel_ms(s3, steps)
     gps = 128 ** 3 * steps
     out["gpe3d_128cube_200steps_c64"] = {"kernel_ms": ms, "grid_point_steps_per_s": gps / (ms * 1e-3),
-                                         "hbm_equivalent_GBps_4_passes": gps * 64 / (ms * 1e-3) / 1e9}
+                                         "hbm_equivalent_GBps_4_passes": gps * 64 / (ms * 1e-3) / 1e9,
+                                         "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
     s3.close()
     # streaming mode of the batched workload (one launch per time step)
     insts, psis, _ = W.batch_1d(count=COUNT, h=DT, steps=STEPS)
@@ -235,6 +236,28 @@ def extra_measurements(hfs, W, torch):
     out["batch65536_streaming_hbm"] = hbm_streaming_measurement(hfs, W)
     out["surrogate_fno"] = surrogate_measurement()
     return out
+
+
+def gpe3d_error(hfs, s32, inst, psi0, steps):
+    """psi(T) of the complex64 3D solve from psi0 against the same solve in
+    FP64 on the device (the 128^3 grid is beyond the oracle; the FP64 path is
+    pinned to the oracle at 32^3 and 64^3 by the GPU tests)."""
+    s32.set_time(0.0)
+    s32.set_psi(psi0.ravel())
+    s32.step(steps)
+    u32 = np.asarray(s32.get_psi()).astype(np.complex128)
+    n32 = float(s32.norm()[0])
+    s64 = hfs.Solver([inst], dim=3, precision="c128", chunk_steps=steps)
+    s64.set_schedule(inst.h, "strang", hfs.HFS_FLOW_CF4)
+    s64.set_psi(psi0.ravel())
+    s64.step(steps)
+    u64 = np.asarray(s64.get_psi())
+    n64 = float(s64.norm()[0])
+    s64.close()
+    T = steps * inst.h
+    err = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
+    return {"rel_l2_vs_fp64_device": err, "bound": 1e-5 * max(T, 1.0), "within_bound": err <= 1e-5 * max(T, 1.0),
+            "norm_drift_c64": abs(n32 - 1.0), "norm_drift_c128": abs(n64 - 1.0)}
 
 
 def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
