@@ -30,8 +30,9 @@ __device__ __forceinline__ double frac_turns(double m2, double c, double /*unuse
 }
 
 // sin theta and cos theta - 1 for theta = 2 pi f, |f| <= 1/8 (plus
-// rounding).  Polynomials in t2 = theta^2 of degree 3 (sin / theta) and 4
-// ((cos - 1) / theta^2), near-minimax on |theta| <= pi/4: fitted by
+// rounding).  sin / theta and (cos - 1) / theta^2 as polynomials of degree
+// 3 in t2 = theta^2 (sin of degree 7, cos - 1 of degree 8 in theta),
+// near-minimax on |theta| <= pi/4: fitted by
 // Lawson-reweighted least squares on Chebyshev nodes for the relative error,
 // the coefficients rounded to FP32 one at a time with the later ones refitted.
 // Relative error <= 4.0e-9 (sin) and <= 8.9e-10 (cos - 1), well below FP32
