@@ -61,3 +61,20 @@ def test_invalid_arguments_rejected_on_host(built):
     assert L.hfs_create(ctypes.byref(h), 1, hfs.HFS_C64, arr, 1) == 1
     assert L.hfs_create(ctypes.byref(h), 2, hfs.HFS_C64, arr, 1) == 2
     assert L.hfs_create(None, 1, hfs.HFS_C64, arr, 1) == 1
+    # 1D grids are powers of two from 128 to 4096
+    for n in (64, 8192):
+        arr = hfs.make_instances([{"n": [n], "a": [-1.0], "b": [1.0]}])
+        assert L.hfs_create(ctypes.byref(h), 1, hfs.HFS_C64, arr, 1) == 2
+    ok = {"n": [256], "a": [-1.0], "b": [1.0]}
+    arr = hfs.make_instances([ok])
+    assert L.hfs_create(ctypes.byref(h), 1, 7, arr, 1) == 1                # precision
+    assert L.hfs_create(ctypes.byref(h), 1, hfs.HFS_C64, arr, 0) == 1      # empty batch
+    for bad in ({"omega_law": 4}, {"vi_kind": 3}):
+        arr = hfs.make_instances([dict(ok, **bad)])
+        assert L.hfs_create(ctypes.byref(h), 1, hfs.HFS_C64, arr, 1) == 1
+    # 3D: one instance per context, centred boxes
+    d3 = {"n": [32, 32, 32], "a": [-6.0] * 3, "b": [6.0] * 3}
+    arr = hfs.make_instances([d3, d3])
+    assert L.hfs_create(ctypes.byref(h), 3, hfs.HFS_C64, arr, 2) == 2
+    arr = hfs.make_instances([dict(d3, a=[-5.0, -6.0, -6.0], b=[7.0, 6.0, 6.0])])
+    assert L.hfs_create(ctypes.byref(h), 3, hfs.HFS_C64, arr, 1) == 2

@@ -347,6 +347,43 @@ def test_errors_reported():
     assert s.status() == 0  # cleared
 
 
+def test_bind_and_step_preconditions():
+    """Buffers must be 256-byte aligned and the workspace large enough for the
+    chunk; stepping needs bound buffers and a schedule.  Each refusal leaves
+    the context usable."""
+    need_gpu()
+    import ctypes
+    import torch
+    from paper_1007_3470_gb300 import hfs
+    L = hfs.lib()
+    insts, psis, _ = W.batch_1d(count=6, seed=3)
+    arr = hfs.make_instances(insts)
+    h = ctypes.c_void_p()
+    assert L.hfs_create(ctypes.byref(h), 1, hfs.HFS_C64, arr, len(insts)) == 0
+    try:
+        assert L.hfs_step(h, ctypes.c_int64(1)) == 6                    # nothing bound
+        elems, _ = hfs.hfs_state_size(h)
+        chunk = 16
+        wbytes = hfs.hfs_workspace_size(h, chunk)
+        psi = torch.zeros(elems + 64, dtype=torch.complex64, device="cuda")
+        work = torch.empty(wbytes + 512, dtype=torch.uint8, device="cuda")
+        p0, w0 = psi.data_ptr(), work.data_ptr()
+        assert p0 % 256 == 0 and w0 % 256 == 0
+        bind = lambda p, w, nb: L.hfs_bind(h, ctypes.c_void_p(p), ctypes.c_void_p(w), ctypes.c_size_t(nb),
+                                           ctypes.c_int64(chunk))
+        assert bind(p0 + 8, w0, wbytes) == 7                             # psi misaligned
+        assert bind(p0, w0 + 128, wbytes) == 7                           # workspace misaligned
+        assert bind(p0, w0, wbytes - 1) == 8                             # workspace too small
+        assert bind(p0, w0, wbytes) == 0
+        assert L.hfs_step(h, ctypes.c_int64(1)) == 6                     # no schedule yet
+        hfs.hfs_set_schedule(h, hfs.HFS_SPLIT_HO, hfs.HFS_FLOW_CF4, hfs.HFS_COMP_STRANG, 0.005)
+        assert L.hfs_step(h, ctypes.c_int64(-1)) == 1
+        assert L.hfs_step(h, ctypes.c_int64(3)) == 0
+        assert L.hfs_sync_status(h) == 0
+    finally:
+        L.hfs_destroy(h)
+
+
 @pytest.mark.parametrize("graphs", [False, True])
 def test_profiling_events(graphs):
     """The step-kernel timing hook works with and without graph replay."""
