@@ -19,7 +19,7 @@ import math
 import os
 import subprocess
 from dataclasses import dataclass, field
-from typing import Sequence
+from typing import Optional, Sequence
 
 import numpy as np
 
@@ -174,6 +174,9 @@ class Problem:
     h: float = 0.01
     t0: float = 0.0
     naive_dft: bool = False
+    # explicit composition coefficients (a[m], b[m+1], b_1 applied first)
+    # instead of a named scheme
+    coeffs: Optional[tuple] = None
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -202,7 +205,9 @@ class Problem:
         p.sigma = self.sigma
         p.split = self.split
         p.ho_flow = self.ho_flow
-        a, b = composition(self.scheme)
+        a, b = composition(self.scheme) if self.coeffs is None else (list(self.coeffs[0]), list(self.coeffs[1]))
+        if len(b) != len(a) + 1:
+            raise ValueError("a composition has m a's and m + 1 b's")
         av = np.ascontiguousarray(a, dtype=np.float64)
         bv = np.ascontiguousarray(b, dtype=np.float64)
         self._keep[:] = [av, bv]

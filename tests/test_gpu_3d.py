@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 def _gpu3d(inst, psi0, steps, precision, chunk=512):
     from paper_1007_3470_gb300 import hfs
     s = hfs.Solver([inst], dim=3, precision=precision, chunk_steps=chunk)
-    s.set_schedule(inst.h, inst.scheme, inst.ho_flow)
+    s.set_schedule(inst.h, inst.scheme, inst.ho_flow, inst.split)
     s.set_psi(psi0.ravel())
     s.step(steps)
     out = s.split(s.get_psi())[0]
@@ -79,3 +79,36 @@ def test_3d_128_plane_kernels_per_perturbation(vi_kind, eps):
     assert abs(n32 - 1.0) < 3e-6
     ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
     assert O.rel_l2(o64, ref) <= TOL_C128 * max(T, 1.0)
+
+
+@pytest.mark.parametrize("flow,split,law", [(W.FLOW_M6, W.SPLIT_HO, None), (W.FLOW_CF4, W.SPLIT_FOURIER, None),
+                                            (W.FLOW_LEMMA2, W.SPLIT_HO, W.OMEGA_CONST)])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_3d_schedule_variants_vs_oracle(precision, tol, flow, split, law):
+    """3D with the sixth-order Magnus + Theorem 1 flow, the Fourier split, and
+    the exact flow (Lemma 2) of a constant trap, against the oracle."""
+    need_gpu()
+    import dataclasses
+    inst, psi0, _ = W.gpe_3d(n=32, h=0.005)
+    inst = dataclasses.replace(inst, ho_flow=flow, split=split)
+    if law is not None:
+        inst = dataclasses.replace(inst, omega_law=law)
+    steps = 16
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    out, nrm, _ = _gpu3d(inst, psi0, steps, precision)
+    assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+    assert abs(nrm - 1.0) < (1e-12 if precision == "c128" else 3e-6)
+
+
+def test_3d_128_fourier_split_plane_vs_fp64():
+    """The 128^3 complex64 plane kernels under the Fourier split (trap in the
+    x-phase) agree with the FP64 line passes."""
+    need_gpu()
+    import dataclasses
+    inst, psi0, _ = W.gpe_3d(n=128, h=0.005)
+    inst = dataclasses.replace(inst, split=W.SPLIT_FOURIER)
+    steps = 4
+    o32, n32, _ = _gpu3d(inst, psi0, steps, "c64")
+    o64, _, _ = _gpu3d(inst, psi0, steps, "c128")
+    assert O.rel_l2(o32, o64) <= TOL_C64 * max(steps * inst.h, 1.0) * 0.1
+    assert abs(n32 - 1.0) < 3e-6
