@@ -3,7 +3,7 @@
  * split-step solver (the learned map from an initial state and the problem
  * parameters to the state at a fixed final time; the paper has no learned
  * component -- the surrogate is trained on trajectories of this library's
- * Hermite-Fourier solver, which stays the fallback and the judge of its
+ * Hermite-Fourier solver, which stays the fallback and the reference for its
  * error).
  *
  * Architecture (channels last, one sample = `grid` points):

@@ -25,7 +25,7 @@ def test_surrogate_trains_and_is_judged_against_the_solver():
     err = S.rel_errors(S.predict(m, Xte, 512), Yte)
     med = float(np.median(err))
     assert med < 0.1
-    # the judge: the plain solver at the surrogate's accuracy
+    # the comparison: the plain solver at the surrogate's accuracy
     dt, solver_med = S.equal_accuracy_solver(te_i, te_p, Yte, med)
     assert solver_med <= med and 0 < dt <= 0.5
     fno_rate = S.time_inference(m, Xte)
