@@ -218,6 +218,37 @@ def test_batched_mixed_sizes(precision, tol):
     assert sorted({i.n[0] for i in insts}) == [128, 256, 512, 1024, 2048, 4096]
 
 
+@pytest.mark.parametrize("flow,split", [(W.FLOW_M6, W.SPLIT_HO), (W.FLOW_CF4, W.SPLIT_FOURIER)])
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_batched_mixed_sizes_flows_and_splits(precision, tol, flow, split):
+    """The batched workload (every size, the per-perturbation kernel) under
+    the sixth-order Magnus flow and under the Fourier split, instance by
+    instance against the oracle."""
+    need_gpu()
+    import dataclasses
+    insts, psis, _ = W.batch_1d(count=24, seed=17)
+    insts = [dataclasses.replace(i, ho_flow=flow, split=split) for i in insts]
+    steps = 40
+    refs = O.run_batch([O.Problem(**i.as_dict()) for i in insts], psis, steps)
+    outs = _run_gpu(insts, psis, steps, precision, 0.005, flow=flow, split=split)
+    errs = [O.rel_l2(o, r) for o, r in zip(outs, refs)]
+    assert max(errs) <= budget(tol, steps * 0.005), max(errs)
+    assert sorted({i.n[0] for i in insts}) == [128, 256, 512, 1024, 2048, 4096]
+
+
+def test_streaming_fp64_matches_resident():
+    """The FP64 (complex128) step kernel in streaming launches of one and
+    three steps gives bitwise the resident result."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=30, seed=23)
+    steps = 7
+    base = _run_gpu(insts, psis, steps, "c128", 0.005)
+    for mode in ((hfs.HFS_MODE_STREAMING, 1), (hfs.HFS_MODE_STREAMING, 3)):
+        out = _run_gpu(insts, psis, steps, "c128", 0.005, mode=mode)
+        assert all(np.array_equal(a, b) for a, b in zip(base, out))
+
+
 def test_streaming_many_items_per_cta():
     """With far more work items than CTAs (every CTA takes several items per
     launch, every plan size present), streaming launches of one and two
