@@ -131,17 +131,19 @@ template <bool PK> __device__ __forceinline__ float2 fma2(float2 a, float2 b, fl
     else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 }
 
-// small_rotation for two angles in packed FP32
-__device__ __forceinline__ void small_rotation2(float2 f, float2 &sn, float2 &cm1)
+// small_rotation for two angles in packed FP32; cm1 comes out multiplied by
+// cs, a power of two folded into the polynomial's coefficients (every Horner
+// step scales exactly, so cm1 cs rounds exactly as cm1 times cs would)
+__device__ __forceinline__ void small_rotation2(float2 f, float2 &sn, float2 &cm1, float cs = 1.0f)
 {
     const float2 th = __fmul2_rn(f, bc2(6.28318530717958647692f));
     const float2 t2 = __fmul2_rn(th, th);
     float2 ps = __ffma2_rn(t2, bc2(kSin7), bc2(kSin5));
     ps = __ffma2_rn(ps, t2, bc2(kSin3));
     sn = __ffma2_rn(__fmul2_rn(th, t2), ps, th);
-    float2 pc = __ffma2_rn(t2, bc2(kCos8), bc2(kCos6));
-    pc = __ffma2_rn(pc, t2, bc2(kCos4));
-    pc = __ffma2_rn(pc, t2, bc2(kCos2));
+    float2 pc = __ffma2_rn(t2, bc2(kCos8 * cs), bc2(kCos6 * cs));
+    pc = __ffma2_rn(pc, t2, bc2(kCos4 * cs));
+    pc = __ffma2_rn(pc, t2, bc2(kCos2 * cs));
     cm1 = __fmul2_rn(t2, pc);
 }
 
@@ -169,14 +171,15 @@ __device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Tur
     const float2 f = add2<PK>(fma2<PK>(q, bc2(-0.25f), t.r), t.c);
     float2 sn, cm1;
     if constexpr (PK) {
-        small_rotation2(f, sn, cm1);
+        small_rotation2(f, sn, cm1, scale);
+        if (scale != 1.0f) sn = __fmul2_rn(sn, bc2(scale));  // folded away for the unscaled x-phase
     } else {
         small_rotation(f.x, sn.x, cm1.x);
         small_rotation(f.y, sn.y, cm1.y);
-    }
-    if (scale != 1.0f) {  // folded away for the unscaled x-phase
-        sn = mul2<PK>(sn, bc2(scale));
-        cm1 = mul2<PK>(cm1, bc2(scale));
+        if (scale != 1.0f) {
+            sn = mul2<PK>(sn, bc2(scale));
+            cm1 = mul2<PK>(cm1, bc2(scale));
+        }
     }
     u0 = finish_rotation(u0, __float_as_int(tq.x) & 3, sn.x, cm1.x, scale);
     u1 = finish_rotation(u1, __float_as_int(tq.y) & 3, sn.y, cm1.y, scale);
