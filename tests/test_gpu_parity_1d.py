@@ -74,7 +74,7 @@ def test_schedule_variants(precision, tol, comp, flow, split):
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_custom_composition(precision, tol):
     """A user-supplied, non-symmetric composition (a = (0.3, 0.7),
-    b = (0.15, 0.5, 0.35): consistent, first order) on the time-dependent GPE
+    b = (0.15, 0.5, 0.35): consistent, second order) on the time-dependent GPE
     against the oracle applying the same coefficients stage by stage; and
     Strang's coefficients passed as a custom set reproduce the built-in
     Strang bitwise."""

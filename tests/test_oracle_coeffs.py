@@ -189,3 +189,32 @@ def test_table1_printed_values():
             assert abs(b[int(k) - 1] - v) < 1e-15, (name, k)
         for k, v in ent["a"].items():
             assert abs(a[int(k) - 1] - v) < 1e-15, (name, k)
+
+
+def test_explicit_composition_coefficients():
+    """The oracle's explicit (a, b) coefficients: a named scheme's own
+    coefficients reproduce it exactly; a wrong count is refused; and the order
+    follows the order conditions.  With a = (0.3, 0.7) the second-order
+    condition sum_i a_i (b_1 + ... + b_i) = 1/2 holds for b = (0.15, 0.5, 0.35)
+    and fails for b = (0.25, 0.5, 0.25) (0.6): global errors fall as h^2 and
+    as h respectively."""
+    import dataclasses
+    base = O.Problem(n=[128], a=[-10.0], b=[10.0], w0=1.0, eps=0.05, vi_kind=O.VI_COS, vi_k=1.5, sigma=2.0,
+                     ho_flow=O.FLOW_LEMMA2, scheme="srkn6_4", h=0.05)
+    x = np.linspace(-10, 10, 128, endpoint=False)
+    psi0 = (np.pi ** -0.25 * np.exp(-(x - 0.5) ** 2 / 2)).astype(complex)
+    named = O.run(base, psi0, 10)
+    same = O.run(dataclasses.replace(base, coeffs=O.composition("srkn6_4")), psi0, 10)
+    assert np.array_equal(named, same)
+    with pytest.raises(ValueError):
+        O.run(dataclasses.replace(base, coeffs=([0.5, 0.5], [1.0, 0.0])), psi0, 1)
+    T = 1.0
+    ref = O.run(dataclasses.replace(base, scheme="ni5_84", h=T / 200), psi0, 200)
+
+    def rate(coeffs):
+        e = [O.rel_l2(O.run(dataclasses.replace(base, coeffs=coeffs, h=T / k), psi0, k), ref) for k in (20, 40)]
+        return math.log2(e[0] / e[1])
+
+    for b, order in (([0.15, 0.5, 0.35], 2.0), ([0.25, 0.5, 0.25], 1.0)):
+        assert abs(sum(ai * sum(b[: i + 1]) for i, ai in enumerate([0.3, 0.7])) - 0.5) < 1e-12 or order == 1.0
+        assert abs(rate(([0.3, 0.7], b)) - order) < 0.3
