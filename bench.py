@@ -201,9 +201,23 @@ def extra_measurements(hfs, W, torch):
     s3.set_psi(psi0.ravel())
     ms = kernel_ms(s3, steps)
     gps = 128 ** 3 * steps
+    # algorithmic traffic: two global round trips of the complex64 state per
+    # sub-stage (the z-pass and the plane pass), 32 B per grid-point-step
+    peaks, _ = _peaks()
+    hbm3 = gps * 32 / (ms * 1e-3) / 1e9
     out["gpe3d_128cube_200steps_c64"] = {"kernel_ms": ms, "grid_point_steps_per_s": gps / (ms * 1e-3),
-                                         "hbm_equivalent_GBps_4_passes": gps * 64 / (ms * 1e-3) / 1e9,
+                                         "hbm_equivalent_GBps_32B": hbm3,
+                                         "hbm_equivalent_frac_of_measured": hbm3 / float(peaks.get("hbm_gbs", 6800.0)),
                                          "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
+    # the same with the z-transforms' radix-16 stages on the tensor cores
+    s3.set_dft_engine(hfs.HFS_DFT_TENSOR_3XTF32)
+    s3.set_time(0.0)
+    s3.set_psi(psi0.ravel())
+    ms_tc = kernel_ms(s3, steps)
+    out["gpe3d_128cube_200steps_c64_tensor_dft"] = {
+        "kernel_ms": ms_tc, "grid_point_steps_per_s": gps / (ms_tc * 1e-3),
+        "dft_stages": "radix-16 z-pass stages as 3xTF32 tcgen05 matrix products",
+        "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
     s3.close()
     # streaming mode of the batched workload (one launch per time step)
     insts, psis, _ = W.batch_1d(count=COUNT, h=DT, steps=STEPS)
@@ -236,6 +250,21 @@ def extra_measurements(hfs, W, torch):
     out["batch65536_streaming_hbm"] = hbm_streaming_measurement(hfs, W)
     out["surrogate_fno"] = surrogate_measurement()
     return out
+
+
+def unprojected_drift(hfs, insts, psis, steps):
+    """Relative norm change of every instance of the batch over one solve with
+    the norm projection off (device norms, FP64 accumulation): the FP32
+    rounding drift, a zero-mean random walk (signed mean next to rms and max)."""
+    s = hfs.Solver(insts, precision="c64", chunk_steps=steps)
+    s.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    s.set_psi(psis)
+    n0 = s.norm()
+    s.step(steps)
+    d = s.norm() / n0 - 1.0
+    s.close()
+    return {"max_abs": float(np.abs(d).max()), "rms": float(np.sqrt(np.mean(d * d))), "mean": float(d.mean()),
+            "instances": len(insts)}
 
 
 def gpe3d_error(hfs, s32, inst, psi0, steps):
@@ -280,7 +309,22 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
         s.step(steps)
         best = min(best, hfs.hfs_last_step_kernel_ms(s.h))
     st = s.status()
+    # the result of one solve from psi0 against the FP64 oracle on two
+    # instances of every grid size
+    s.set_time(0.0)
+    s.set_psi(psis)
+    s.step(steps)
+    out = s.split(s.get_psi())
     s.close()
+    from oracle import oracle as O
+    pick, seen = [], {}
+    for i, inst in enumerate(insts):
+        if seen.get(inst.n[0], 0) < 2:
+            seen[inst.n[0]] = seen.get(inst.n[0], 0) + 1
+            pick.append(i)
+    refs = O.run_batch([O.Problem(**insts[i].as_dict()) for i in pick], [psis[i] for i in pick], steps)
+    errs = [O.rel_l2(out[i], r) for i, r in zip(pick, refs)]
+    bound = 1e-5 * max(steps * DT, 1.0)
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     gbps = pts * steps * 16.0 / (best * 1e-3) / 1e9
@@ -289,7 +333,9 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
             "ms_per_launch": best / steps, "grid_point_steps_per_s": pts * steps / (best * 1e-3),
             "hbm_GBps_algorithmic": gbps, "hbm_frac_of_measured": gbps / hbm,
             "algorithmic_bytes_per_launch": pts * 16, "dram_bytes_per_launch": traffic, "plans_ept": tuned,
-            "status": st}
+            "status": st,
+            "error": {"rel_l2_max": float(max(errs)), "bound": bound, "within_bound": bool(max(errs) <= bound),
+                      "instances": len(pick), "vs": "FP64 oracle"}}
 
 
 def surrogate_measurement():
@@ -339,6 +385,7 @@ def run_native(args):
     gps, flops = algorithmic_counts(insts, STEPS_)
     solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS_)
     solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    solver.set_norm_projection(not args.no_projection)
     tuned = solver.autotune(trial_steps=20) if args.autotune else None
     hfs.hfs_set_profiling(solver.h, True)
     solver.set_graphs(True)
@@ -410,6 +457,7 @@ def run_native(args):
         "config": {"workload": workload, "instances": COUNT_, "time_steps": STEPS_,
                    "dt": DT, "grid_sizes": "128..4096 uniform", "composition": "strang", "ho_flow": "magnus4_cf+thm2",
                    "mode": "resident, graph-replayed", "l2": "flushed between steps (256 MiB write)",
+                   "norm_projection": not args.no_projection,
                    "solves_per_s": ws * args.steps / (total_ms * 1e-3),
                    "plans_ept": tuned},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
@@ -430,6 +478,7 @@ def run_native(args):
     }
     if rank == 0 and not args.no_extras:
         line["extras"] = extra_measurements(hfs, W, torch)
+        line["extras"]["norm_drift_without_projection"] = unprojected_drift(hfs, insts, psis, STEPS_)
     if rank == 0 and not args.no_cpu_baseline:
         # the e2e solves started from psi0 of this batch: pinned_out holds psi(T)
         same = COUNT_ == COUNT and STEPS_ == STEPS and rank_seed(rank) == 20100703
@@ -468,8 +517,10 @@ def result_error(gpu_state: np.ndarray, sizes, pick, psis0, refs) -> dict:
         errs.append(np.linalg.norm(g - r) / np.linalg.norm(r))
         drift.append(abs(np.sum(np.abs(g) ** 2) - np.sum(np.abs(p0) ** 2)) / np.sum(np.abs(p0) ** 2))
     T = STEPS * DT
+    bound, dbound = 1e-5 * max(T, 1.0), 1e-6
     return {"rel_l2_max": float(np.max(errs)), "rel_l2_median": float(np.median(errs)),
-            "bound": 1e-5 * max(T, 1.0), "within_bound": bool(np.max(errs) <= 1e-5 * max(T, 1.0)),
+            "bound": bound, "norm_drift_bound": dbound,
+            "within_bound": bool(np.max(errs) <= bound and np.max(drift) <= dbound),
             "norm_drift_max": float(np.max(drift)), "norm_drift_median": float(np.median(drift)),
             "instances": len(errs), "vs": "FP64 oracle"}
 
@@ -506,6 +557,8 @@ def run_case(args):
         inst, psi0, steps = W.gpe_3d(n=128, h=0.005, steps=args.time_steps)
         s3 = hfs.Solver([inst], dim=3, precision="c64", chunk_steps=steps)
         s3.set_schedule(inst.h, "strang", hfs.HFS_FLOW_CF4)
+        if args.tensor_dft:
+            s3.set_dft_engine(hfs.HFS_DFT_TENSOR_3XTF32)
         hfs.hfs_set_profiling(s3.h, True)
         s3.set_psi(psi0.ravel())
         for _ in range(args.warmup):
@@ -515,7 +568,7 @@ def run_case(args):
             s3.step(steps)
             ms.append(hfs.hfs_last_step_kernel_ms(s3.h))
         s3.close()
-        print(json.dumps({"case": "3d", "n": 128, "time_steps": steps, "kernel_ms": ms,
+        print(json.dumps({"case": "3d", "n": 128, "time_steps": steps, "tensor_dft": args.tensor_dft, "kernel_ms": ms,
                           "grid_point_steps_per_s": 128 ** 3 * steps / (min(ms) * 1e-3)}))
     elif args.case == "fno":
         from paper_1007_3470_gb300 import surrogate as S
@@ -590,10 +643,14 @@ def main():
                     help="instances per grid size in each step of --impl reference (about 2 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-projection", action="store_true",
+                    help="run the headline solve without the norm projection")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
     ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
+    ap.add_argument("--tensor-dft", action="store_true",
+                    help="--case 3d: the z-transforms' radix-16 stages on the tensor cores")
     ap.add_argument("--case", choices=["3d", "fno", "hbm"], default=None,
                     help="run one secondary workload alone (profiling)")
     args = ap.parse_args()

@@ -156,6 +156,34 @@ int hfs_set_schedule(hfs_ctx_t ctx, int split, int ho_flow, int composition, con
  * HFS_MODE_STREAMING, the number of steps fused per launch (>= 1). */
 int hfs_set_mode(hfs_ctx_t ctx, int mode, int steps_per_launch);
 
+/* Norm projection of the 1D complex64 step (enable != 0; default off).  The
+ * exact scheme conserves the discrete norm dx sum |psi_j|^2 (every sub-flow is
+ * a pure phase in x or k: Lemma 1, Eq. GP1ODE_T), but FP32 rounding in the
+ * FFT passes and phases changes it by small unbiased amounts that add up as
+ * a random walk (rms ~ 8e-7 after 500 steps for a state covering ~15 grid
+ * points).  With projection on, each sub-stage rescales every instance by
+ * sqrt(N0 / N_j), N_0 the sum of |psi|^2 at the start of the hfs_step() call
+ * and N_j the current one (both measured in FP32 inside the fused kernel),
+ * which removes the radial component of the rounding error instead of
+ * letting it accumulate; the paper's method itself has no such step.
+ * Errors: HFS_ERR_UNSUPPORTED for 3D or complex128 contexts (their drift is
+ * ~1e-8 and ~1e-14). */
+int hfs_set_norm_projection(hfs_ctx_t ctx, int enable);
+
+/* Engine of the radix-16 DFT stages of the 3D z-transform (the first pass of
+ * each forward and inverse FFT along z, Eq. GP1ODE_T), complex64 with n = 64
+ * or 128 per axis:
+ *   HFS_DFT_SIMT          butterflies on the FP32 pipes (default);
+ *   HFS_DFT_TENSOR_3XTF32 each CTA's 256 length-16 DFTs as one real matrix
+ *                         product on the tensor cores (tcgen05), operands
+ *                         split into two TF32 parts, three products
+ *                         accumulated in FP32.
+ * Errors: HFS_ERR_INVALID_ARG (unknown engine), HFS_ERR_UNSUPPORTED (1D,
+ * complex128, or another grid size). */
+#define HFS_DFT_SIMT 0
+#define HFS_DFT_TENSOR_3XTF32 1
+int hfs_set_dft_engine(hfs_ctx_t ctx, int engine);
+
 /* Capture each hfs_step(nsteps) launch sequence in a CUDA graph and replay
  * it on later calls with the same nsteps (enable != 0).  Capture needs a
  * stream other than the legacy default stream: hfs_step() returns
@@ -244,7 +272,10 @@ int hfs_last_step_kernel_ms(hfs_ctx_t ctx, float *ms);
  * be serialised by the caller.
  *
  * wait != 0: synchronise the stream before returning and report a non-finite
- * state as HFS_ERR_NONFINITE.  Errors: HFS_ERR_WORKSPACE when count exceeds
+ * state as HFS_ERR_NONFINITE.  With wait == 0 the call returns once the work
+ * is enqueued, and device-side problems (a non-finite state) are not
+ * reported to the caller: the status word that records them lives in the
+ * shared array and is cleared by the next call.  Errors: HFS_ERR_WORKSPACE when count exceeds
  * HFS_NOALLOC_MAX_INSTANCES; HFS_ERR_INVALID_ARG, HFS_ERR_UNSUPPORTED,
  * HFS_ERR_ALIGNMENT, HFS_ERR_STEP_TOO_LARGE, HFS_ERR_CUDA as for the
  * context API. */

@@ -92,7 +92,7 @@ double omega_bound(const hfs_instance &p, double t0, double t1)
 namespace {
 
 struct Layout {
-    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, nodes, rec, diag, total;
+    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, nodes, rec, diag, norm, total;
 };
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -123,6 +123,8 @@ struct hfs_ctx_s {
     // execution
     int mode = HFS_MODE_RESIDENT, spl = 1;
     bool graphs = false;
+    bool norm_projection = false;  // 1D complex64: hfs_set_norm_projection
+    int dft_engine = HFS_DFT_SIMT;  // 3D complex64: hfs_set_dft_engine
     cudaStream_t stream = nullptr;
     // bound buffers
     void *psi = nullptr;
@@ -186,6 +188,7 @@ Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
     L.nodes = take(law_nodes_bytes(nstage));
     L.rec = take(recsz * c->count * (nstage + 1));
     L.diag = take(sizeof(double) * 2 * std::max<int64_t>(c->count, 1));
+    L.norm = take(sizeof(float) * std::max<int64_t>(c->count, 1));
     L.total = o;
     return L;
 }
@@ -299,6 +302,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
             a.ticket = ticket;
             a.status = status;
+            a.norm_target = wptr<float>(c, c->lay.norm);
             const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64, c->variant)));
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
             if (c->profiling && done == 0) CK(record_prof(c, 0));
@@ -307,6 +311,8 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
                 a.j0 = s0 * m;
                 a.j1 = s1 * m;
                 a.final_x = (s1 == S) ? 1 : 0;
+                // the first launch of the call records the norm it projects onto
+                a.proj = !c->norm_projection ? PROJ_OFF : (done == 0 && s0 == 0) ? PROJ_SET : PROJ_USE;
                 CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
                 CK(launch_step1d(fp64, c->variant, a, grid, c->stream));
             }
@@ -322,6 +328,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.status = status;
             a.n = c->inst[0].n[0];
             a.vi = c->inst[0].eps != 0.0 ? c->inst[0].vi_kind : HFS_VI_NONE;
+            a.dft_tc = c->dft_engine == HFS_DFT_TENSOR_3XTF32 ? 1 : 0;
             if (c->profiling && done == 0) CK(record_prof(c, 0));
             CK(launch_step3d(fp64, a, c->stream));
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
@@ -580,6 +587,26 @@ int hfs_set_mode(hfs_ctx_t c, int mode, int spl)
     if (!c || (mode != HFS_MODE_RESIDENT && mode != HFS_MODE_STREAMING) || spl < 1) return HFS_ERR_INVALID_ARG;
     c->mode = mode;
     c->spl = spl;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+int hfs_set_norm_projection(hfs_ctx_t c, int enable)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    if (c->dim != 1 || c->precision != HFS_C64) return HFS_ERR_UNSUPPORTED;
+    c->norm_projection = enable != 0;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+int hfs_set_dft_engine(hfs_ctx_t c, int engine)
+{
+    if (!c || (engine != HFS_DFT_SIMT && engine != HFS_DFT_TENSOR_3XTF32)) return HFS_ERR_INVALID_ARG;
+    if (engine == HFS_DFT_TENSOR_3XTF32 &&
+        (c->dim != 3 || c->precision != HFS_C64 || (c->inst[0].n[0] != 64 && c->inst[0].n[0] != 128)))
+        return HFS_ERR_UNSUPPORTED;
+    c->dft_engine = engine;
     drop_graphs(c);
     return HFS_OK;
 }

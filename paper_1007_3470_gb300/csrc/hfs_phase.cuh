@@ -163,26 +163,33 @@ template <bool PK> __device__ __forceinline__ Turns2 frac_turns2(float2 m2, floa
     }
 }
 
-template <bool PK>
-__device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Turns2 t, float scale)
+//
+// scale: a compile-time power of two (folded into the polynomial); C: a
+// run-time factor near 1 (the norm projection of the k-phase), applied as
+// u C scale + u (cm1 - i sn) C scale; C = 1 gives bit-identical results to
+// the unprojected form.
+template <bool PK, bool CORR = false>
+__device__ __forceinline__ void apply_turns2(cpx<float> &u0, cpx<float> &u1, Turns2 t, float scale, float C = 1.0f)
 {
     const float2 tq = fma2<PK>(bc2(4.0f), add2<PK>(t.r, t.c), bc2(kRoundMagic));
     const float2 q = add2<PK>(tq, bc2(-kRoundMagic));
     const float2 f = add2<PK>(fma2<PK>(q, bc2(-0.25f), t.r), t.c);
     float2 sn, cm1;
+    const float sc = CORR ? scale * C : scale;  // exact: scale is a power of two
     if constexpr (PK) {
         small_rotation2(f, sn, cm1, scale);
-        if (scale != 1.0f) sn = __fmul2_rn(sn, bc2(scale));  // folded away for the unscaled x-phase
+        if (CORR || scale != 1.0f) sn = __fmul2_rn(sn, bc2(sc));  // folded away for the unscaled x-phase
+        if constexpr (CORR) cm1 = __fmul2_rn(cm1, bc2(C));
     } else {
         small_rotation(f.x, sn.x, cm1.x);
         small_rotation(f.y, sn.y, cm1.y);
-        if (scale != 1.0f) {
-            sn = mul2<PK>(sn, bc2(scale));
-            cm1 = mul2<PK>(cm1, bc2(scale));
+        if (CORR || scale != 1.0f) {
+            sn = mul2<PK>(sn, bc2(sc));
+            cm1 = mul2<PK>(cm1, bc2(sc));
         }
     }
-    u0 = finish_rotation(u0, __float_as_int(tq.x) & 3, sn.x, cm1.x, scale);
-    u1 = finish_rotation(u1, __float_as_int(tq.y) & 3, sn.y, cm1.y, scale);
+    u0 = finish_rotation(u0, __float_as_int(tq.x) & 3, sn.x, cm1.x, sc);
+    u1 = finish_rotation(u1, __float_as_int(tq.y) & 3, sn.y, cm1.y, sc);
 }
 
 // One-part form in packed FP32: the phase summed first, then the quarter turn

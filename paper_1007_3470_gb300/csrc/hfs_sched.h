@@ -60,7 +60,10 @@ struct Step1DArgs {
     const void *tw;                 // twiddle table (cpx<R>)
     unsigned *ticket;
     unsigned *status;
+    float *norm_target;             // per instance: target sum |u|^2 of the norm projection
+    int32_t proj;                   // PROJ_OFF, PROJ_SET (first launch of a call), PROJ_USE
 };
+enum : int32_t { PROJ_OFF = 0, PROJ_SET = 1, PROJ_USE = 2 };
 // variant: HFS_VI_* when every instance has that perturbation kind and a box
 // symmetric about 0 (FP32 only; from step1d_variant), -1 for the generic kernel
 cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st);

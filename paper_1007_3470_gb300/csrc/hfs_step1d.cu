@@ -117,7 +117,8 @@ __global__ void twiddle_kernel(float4 *tf, double2 *td)
 size_t step1d_smem_bytes(bool fp64)
 {
     if (fp64) return (size_t)step1d_exchange_elems * sizeof(cpx<double>);
-    return (size_t)step1d_exchange_elems * sizeof(cpx<float>) + (size_t)step1d_vtable_floats * sizeof(float);
+    return (size_t)step1d_exchange_elems * sizeof(cpx<float>) +
+           (size_t)(step1d_vtable_floats + step1d_slot_floats) * sizeof(float);
 }
 
 static cudaError_t prepare_diag(bool fp64)

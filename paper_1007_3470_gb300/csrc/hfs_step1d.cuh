@@ -91,9 +91,11 @@ template <int VI> __device__ __forceinline__ float eps_vi(float mf, const TeamPa
 // were evaluated for every point, both branches (7 % of the kernel time).
 // vt: eps V_I at positions t + T e, written once per work item by the same
 // thread (V_I does not depend on time), so no step re-evaluates it.
+// dsum: the sum of |u|^2 over the thread's points before the phase (the
+// phase leaves |u| unchanged), for the norm projection.
 template <int N, int E, int VI>
 __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc, const TeamParams<float> &tp,
-                                       const float *vt)
+                                       const float *vt, float &dsum)
 {
     constexpr int T = N / E;
     constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
@@ -116,6 +118,7 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
         // F = sigma |u|^2 + eps V_I(x)
         const float d0 = v[e].x * v[e].x + v[e].y * v[e].y;
         const float d1 = v[e + 1].x * v[e + 1].x + v[e + 1].y * v[e + 1].y;
+        dsum += d0 + d1;
         float2 F;
         if constexpr (VI == HFS_VI_NONE) F = mul2<PK>(bc2(tp.sigma), make_float2(d0, d1));
         else F = fma2<PK>(bc2(tp.sigma), make_float2(d0, d1), make_float2(vt[t + T * e], vt[t + T * (e + 1)]));
@@ -126,7 +129,7 @@ __device__ __forceinline__ void xphase(cpx<float> (&v)[E], int t, const RecF &rc
 
 template <int N, int E, int VI>
 __device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &rc, const TeamParams<double> &tp,
-                                       const float *)
+                                       const float *, float &)
 {
     constexpr int T = N / E;
 #pragma unroll
@@ -143,8 +146,10 @@ __device__ __forceinline__ void xphase(cpx<double> (&v)[E], int t, const RecD &r
     }
 }
 
-// kinetic phase of drift D_{j+1} with the inverse transform's 1/N
-template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E], int t, const RecF &rc)
+// kinetic phase of drift D_{j+1} with the inverse transform's 1/N and, with
+// CORR, the norm projection's factor C
+template <int N, int E, bool CORR>
+__device__ __forceinline__ void kphase(cpx<float> (&v)[E], int t, const RecF &rc, float C)
 {
     constexpr int T = N / E;
     constexpr bool PK = E >= HFS_PACK_PHASE_MIN_E;
@@ -159,11 +164,12 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<float> (&v)[E
         }
         const float2 mf = make_float2(tf + (float)(T * e - (2 * e < E ? 0 : N)),
                                       tf + (float)(T * (e + 1) - (2 * (e + 1) < E ? 0 : N)));
-        apply_turns2<PK>(v[e], v[e + 1], frac_turns2<PK>(mul2<PK>(mf, mf), rc.ghi, rc.glo), 1.0f / N);
+        apply_turns2<PK, CORR>(v[e], v[e + 1], frac_turns2<PK>(mul2<PK>(mf, mf), rc.ghi, rc.glo), 1.0f / N, C);
     }
 }
 
-template <int N, int E> __device__ __forceinline__ void kphase(cpx<double> (&v)[E], int t, const RecD &rc)
+template <int N, int E, bool CORR>
+__device__ __forceinline__ void kphase(cpx<double> (&v)[E], int t, const RecD &rc, float)
 {
     constexpr int T = N / E;
 #pragma unroll
@@ -176,9 +182,87 @@ template <int N, int E> __device__ __forceinline__ void kphase(cpx<double> (&v)[
 }
 
 // complex elements of the exchange buffers of a CTA (the largest over the
-// plans: E = 16 values per thread), and floats of the eps V_I table after them
+// plans: E = 16 values per thread), and floats of the eps V_I table and of
+// the per-warp norm sums after them
 constexpr int step1d_exchange_elems = (kCtaThreads / (4096 / 16)) * smem_elems(4096);
 constexpr int step1d_vtable_floats = kCtaThreads * 16;
+constexpr int step1d_slot_floats = kCtaThreads / 32;
+
+// Norm projection (FP32 path).  The exact scheme is unitary: every sub-flow
+// preserves the discrete norm dx sum |u|^2 (Lemma 1; the kicks and drifts
+// are pure phases in x and k).  In FP32 each rounding of the FFT passes and
+// phases changes it by an unbiased random amount, so the norm random-walks
+// (rms ~ 8e-7 after 500 steps for a state spread over ~15 grid points).
+// With projection on, every sub-stage measures the team's sum of |u|^2 in
+// the x-phase and rescales the state in the k-phase by
+// C = sqrt(target / sum), target being the sum at the start of the
+// hfs_step() call: the radial (norm) component of the rounding error is
+// removed each sub-stage instead of accumulating.
+//
+// Team sums: teams of T <= 32 threads occupy aligned lane segments and reduce
+// by xor shuffles inside the segment; larger teams reduce per warp, lane 0
+// stores the warp's sum in slots[warp], and the team adds its warps' slots
+// after the next team barrier (the forward FFT has at least one exchange).
+template <int T> __device__ __forceinline__ float team_sum_begin(float s, float *slots)
+{
+    constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if constexpr (T > 32) {
+        if ((threadIdx.x & 31) == 0) slots[threadIdx.x >> 5] = s;
+    }
+    return s;
+}
+template <int T> __device__ __forceinline__ float team_sum_end(float s, const float *slots, int g)
+{
+    if constexpr (T <= 32) {
+        return s;
+    } else {
+        float r = 0.0f;
+#pragma unroll
+        for (int w = 0; w < T / 32; ++w) r += slots[g * (T / 32) + w];
+        return r;
+    }
+}
+
+// sub-stages [j0, j1): X_j, forward FFT, kinetic phase (+ projection), inverse FFT
+template <typename R, int VI, int N, int E, bool PROJ, typename Rec>
+__device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], int t, int g, bool active, int idx,
+                                          const Rec *rec, const TeamParams<R> &tp, cpx<R> *sm,
+                                          const typename TwOf<R>::type *tw, const float *vt, float *slots)
+{
+    constexpr int T = N / E;
+    // the team's target sum of |u|^2: read, or set from the first sub-stage
+    float target = 0.0f;
+    if constexpr (PROJ) {
+        if (a.proj == PROJ_USE) target = active ? a.norm_target[idx] : 0.0f;
+    }
+    for (int64_t j = a.j0; j < a.j1; ++j) {
+        const Rec rc = rec[j];
+        // Position-dependent values (m^2, x, V_I(x)) are the same at every
+        // step; an opaque copy of t makes the compiler recompute them (a few
+        // integer and SFU operations) instead of holding 3E of them live
+        // across the whole time loop.
+        int tl = t;
+        asm volatile("" : "+r"(tl));
+        float dsum = 0.0f;
+        xphase<N, E, VI>(v, tl, rc, tp, vt, dsum);
+        if constexpr (PROJ) dsum = team_sum_begin<T>(dsum, slots);
+        FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
+        float C = 1.0f;
+        if constexpr (PROJ) {
+            const float s = team_sum_end<T>(dsum, slots, g);
+            if (j == a.j0 && a.proj == PROJ_SET) {
+                target = s;
+                if (active && t == 0) a.norm_target[idx] = s;
+            } else if (target > 0.0f && s > 0.0f && isfinite(s)) {
+                C = sqrtf(target / s);
+            }
+        }
+        kphase<N, E, PROJ>(v, tl, rc, C);
+        FftPlan<N, E>::template run<true, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
+    }
+}
 
 template <typename R, int VI, int N, int E>
 __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
@@ -200,29 +284,23 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = active ? psi[t + T * e] : cpx<R>{R(0), R(0)};
     // FP32: the table of eps V_I behind the exchange buffers (each thread
-    // reads back only the entries it wrote)
+    // reads back only the entries it wrote), then the norm-sum slots
     float *vt = reinterpret_cast<float *>(smem + step1d_exchange_elems) + g * N;
+    float *slots = reinterpret_cast<float *>(smem + step1d_exchange_elems) + step1d_vtable_floats;
     if constexpr (sizeof(R) == 4 && VI != HFS_VI_NONE) {
 #pragma unroll
         for (int e = 0; e < E; ++e) vt[t + T * e] = eps_vi<VI>((float)(t + T * e - N / 2), tp);
     }
-
-    for (int64_t j = a.j0; j < a.j1; ++j) {
-        const Rec rc = rec[j];
-        // Position-dependent values (m^2, x, V_I(x)) are the same at every
-        // step; an opaque copy of t makes the compiler recompute them (a few
-        // integer and SFU operations) instead of holding 3E of them live
-        // across the whole time loop.
-        int tl = t;
-        asm volatile("" : "+r"(tl));
-        xphase<N, E, VI>(v, tl, rc, tp, vt);
-        FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
-        kphase<N, E>(v, tl, rc);
-        FftPlan<N, E>::template run<true, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
+    if constexpr (sizeof(R) == 4) {
+        if (a.proj != PROJ_OFF) step_loop<R, VI, N, E, true>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
+        else step_loop<R, VI, N, E, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
+    } else {
+        step_loop<R, VI, N, E, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
     }
     if (a.final_x) {
         const Rec rc = rec[a.j1];
-        xphase<N, E, VI>(v, t, rc, tp, vt);
+        float dsum = 0.0f;
+        xphase<N, E, VI>(v, t, rc, tp, vt, dsum);
     }
     if (active) {
         bool bad = false;

@@ -21,6 +21,7 @@
 #include "hfs_phase.cuh"
 #include "hfs_sched.h"
 #include "hfs_step3d.h"
+#include "hfs_tc.cuh"
 
 namespace hfs {
 
@@ -162,6 +163,87 @@ __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(c
     FftPlan<N, E>::template run<true, R, TX>(v, sm, t, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N * N] = v[e];
+}
+
+// ---------------------------------------------------------------------------
+// z-pass with tensor-core DFT stages (complex64, n = 64 or 128): the first
+// pass of each transform (radix 16, one butterfly per thread) runs as a
+// 3xTF32 matrix product on the tensor cores (hfs_tc.cuh); the exchange, the
+// last pass (radix n/16, twiddles) and the k-phase are those of zpass3d.
+// ---------------------------------------------------------------------------
+template <int N> constexpr size_t zpass_tc_smem()
+{
+    return (size_t)Geo3<N>::TX * N * sizeof(cpx<float>) + 2 * tc::kWBytes + 16;
+}
+
+// the first Stockham pass's exchange (NS = 1, butterfly b = t) after its DFT
+template <int N, int TX> __device__ __forceinline__ void first_pass_exchange(cpx<float> (&v)[16], cpx<float> *sm, int t)
+{
+    constexpr int T = N / 16;
+    cpx<float> *w = sm + (t * 16) * TX;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) w[r * TX] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = sm[(t + T * e) * TX];
+    __syncthreads();
+}
+
+template <int N> __global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(const Step3DArgs a, int64_t j)
+{
+    using GEO = Geo3<N>;
+    constexpr int E = GEO::E, T = GEO::T, TX = GEO::TX;
+    static_assert(GEO::TT == kCtaThreads && E == 16, "one radix-16 butterfly per thread, 256 threads");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *wbuf = smem_raw + (size_t)TX * N * sizeof(cpx<float>);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(wbuf + 2 * tc::kWBytes);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    if (threadIdx.x < 32) tc::alloc(slot);
+    if (threadIdx.x == 0) tc::mbar_init(tc::smem_addr(mbar));
+    tc::fill_w(wbuf, wbuf + tc::kWBytes);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tc::Dft16 st{*slot, tc::smem_addr(wbuf), tc::smem_addr(wbuf + tc::kWBytes), tc::smem_addr(mbar), 0u};
+
+    const int l = threadIdx.x % TX, t = threadIdx.x / TX;
+    const int y = blockIdx.y, x = blockIdx.x * TX + l;
+    cpx<float> *sm = reinterpret_cast<cpx<float> *>(smem_raw) + l;
+    cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)y * N + x;
+    const float4 *tw = reinterpret_cast<const float4 *>(a.tw);
+    cpx<float> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
+    bool ok = tc::dft16<false>(v, st);
+    first_pass_exchange<N, TX>(v, sm, t);
+    stockham_pass<N, E, N / 16, 16, false, true, TX, false>(v, sm, t, tw, 0);
+    {
+        const Rec3F rc = reinterpret_cast<const Rec3F *>(a.rec)[j];
+        const int mx = (x < N / 2) ? x : x - N;
+        const int my = (y < N / 2) ? y : y - N;
+        const float txy = turns_q(mx, rc.g[0], rc.glo[0]) + turns_q(my, rc.g[1], rc.glo[1]);
+        const float scale = 1.0f / ((float)N * (float)N * (float)N);
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+            const int kz0 = t + T * e, kz1 = kz0 + T;
+            const int mz0 = (kz0 < N / 2) ? kz0 : kz0 - N, mz1 = (kz1 < N / 2) ? kz1 : kz1 - N;
+            const Turns2 tz =
+                frac_turns2<true>(make_float2((float)(mz0 * mz0), (float)(mz1 * mz1)), rc.g[2], rc.glo[2]);
+            apply_turns2(v[e], v[e + 1], __fadd2_rn(bc2(txy), __fadd2_rn(tz.r, tz.c)), scale);
+        }
+    }
+    ok = tc::dft16<true>(v, st) && ok;
+    first_pass_exchange<N, TX>(v, sm, t);
+    stockham_pass<N, E, N / 16, 16, true, true, TX, false>(v, sm, t, tw, 0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N * N] = v[e];
+    if (!ok && threadIdx.x == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc::fence_after_sync();
+        tc::dealloc(st.tmem);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -404,13 +486,20 @@ template <typename R, int N> static cudaError_t run3d(const Step3DArgs &a, cudaS
         if ((e = allow_smem(ypass3d<R, N, false>, ts)) != cudaSuccess) return e;
         if ((e = allow_smem(ypass3d<R, N, true>, ts)) != cudaSuccess) return e;
         if ((e = allow_smem(zpass3d<R, N>, ts)) != cudaSuccess) return e;
+        if constexpr (sizeof(R) == 4 && (N == 64 || N == 128))
+            if ((e = allow_smem(zpass3d_tc<N>, zpass_tc_smem<N>())) != cudaSuccess) return e;
         prepared = true;
     }
     const dim3 xg(N * N / GEO::G), tg(N / GEO::TX, N);
     xpass3d<R, N, X_PHASE | X_FWD><<<xg, kCtaThreads, xs, st>>>(a, 0);
     ypass3d<R, N, false><<<tg, GEO::TT, ts, st>>>(a);
     for (int64_t j = 0; j < a.nstage; ++j) {
-        zpass3d<R, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        if constexpr (sizeof(R) == 4 && (N == 64 || N == 128)) {
+            if (a.dft_tc) zpass3d_tc<N><<<tg, GEO::TT, zpass_tc_smem<N>(), st>>>(a, j);
+            else zpass3d<R, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        } else {
+            zpass3d<R, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        }
         ypass3d<R, N, true><<<tg, GEO::TT, ts, st>>>(a);
         if (j + 1 < a.nstage) {
             xpass3d<R, N, X_INV | X_PHASE | X_FWD><<<xg, kCtaThreads, xs, st>>>(a, j + 1);
@@ -457,12 +546,14 @@ template <int VI> static cudaError_t run3d_plane_vi(const Step3DArgs &a, cudaStr
         if ((e = allow_smem(plane3d<MID, VI>, ps)) != cudaSuccess) return e;
         if ((e = allow_smem(plane3d<LAST, VI>, ps)) != cudaSuccess) return e;
         if ((e = allow_smem(zpass3d<float, N>, ts)) != cudaSuccess) return e;
+        if ((e = allow_smem(zpass3d_tc<N>, zpass_tc_smem<N>())) != cudaSuccess) return e;
         prepared = true;
     }
     const dim3 tg(N / GEO::TX, N);
     plane3d<FIRST, VI><<<N, kPlaneThreads, ps, st>>>(a, 0);
     for (int64_t j = 0; j < a.nstage; ++j) {
-        zpass3d<float, N><<<tg, GEO::TT, ts, st>>>(a, j);
+        if (a.dft_tc) zpass3d_tc<N><<<tg, GEO::TT, zpass_tc_smem<N>(), st>>>(a, j);
+        else zpass3d<float, N><<<tg, GEO::TT, ts, st>>>(a, j);
         if (j + 1 < a.nstage) plane3d<MID, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
         else plane3d<LAST, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
     }

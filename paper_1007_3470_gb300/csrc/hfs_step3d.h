@@ -15,6 +15,7 @@ struct Step3DArgs {
     unsigned *status;
     int n;   // points per axis
     int vi;  // perturbation kind in effect (HFS_VI_NONE where eps = 0)
+    int dft_tc;  // complex64, n = 64 / 128: first z-pass radix-16 stages on the tensor cores
 };
 
 struct Diag3DArgs {

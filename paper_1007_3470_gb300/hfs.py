@@ -26,13 +26,14 @@ HFS_SPLIT_HO, HFS_SPLIT_FOURIER = 0, 1
 HFS_FLOW_LEMMA2, HFS_FLOW_CF4, HFS_FLOW_M6 = 0, 1, 2
 HFS_COMP_STRANG, HFS_COMP_SRKN6_4, HFS_COMP_NI4_82, HFS_COMP_NI5_84, HFS_COMP_CUSTOM = 0, 1, 2, 3, 4
 HFS_MODE_RESIDENT, HFS_MODE_STREAMING = 0, 1
+HFS_DFT_SIMT, HFS_DFT_TENSOR_3XTF32 = 0, 1
 
 COMPOSITIONS = {"strang": HFS_COMP_STRANG, "srkn6_4": HFS_COMP_SRKN6_4, "ni4_82": HFS_COMP_NI4_82,
                 "ni5_84": HFS_COMP_NI5_84, "custom": HFS_COMP_CUSTOM}
 
 # every symbol include/hfs.h declares
 EXPORTS = ("hfs_create", "hfs_destroy", "hfs_set_stream", "hfs_state_size", "hfs_instance_offset",
-           "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_graphs",
+           "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_norm_projection", "hfs_set_dft_engine", "hfs_set_graphs",
            "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi", "hfs_step", "hfs_norm",
            "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_autotune", "hfs_set_profiling",
            "hfs_last_step_kernel_ms", "hfs_step1d_noalloc", "hfs_error_string")
@@ -82,6 +83,8 @@ def lib():
             "hfs_bind": [vp, vp, vp, ctypes.c_size_t, i64],
             "hfs_set_schedule": [vp, i32, i32, i32, ctypes.POINTER(dbl), i32, ctypes.POINTER(dbl), i32, dbl],
             "hfs_set_mode": [vp, i32, i32],
+            "hfs_set_norm_projection": [vp, i32],
+            "hfs_set_dft_engine": [vp, i32],
             "hfs_set_graphs": [vp, i32],
             "hfs_set_time": [vp, dbl],
             "hfs_get_time": [vp, ctypes.POINTER(dbl)],
@@ -196,6 +199,14 @@ def hfs_set_schedule(h, split: int, flow: int, composition: int, dt: float,
 
 def hfs_set_mode(h, mode: int, steps_per_launch: int = 1):
     _check(lib().hfs_set_mode(h, mode, steps_per_launch), "hfs_set_mode")
+
+
+def hfs_set_norm_projection(h, enable: bool):
+    _check(lib().hfs_set_norm_projection(h, 1 if enable else 0), "hfs_set_norm_projection")
+
+
+def hfs_set_dft_engine(h, engine: int):
+    _check(lib().hfs_set_dft_engine(h, int(engine)), "hfs_set_dft_engine")
 
 
 def hfs_set_graphs(h, enable: bool):
@@ -322,6 +333,12 @@ class Solver:
 
     def set_graphs(self, enable: bool):
         hfs_set_graphs(self.h, enable)
+
+    def set_norm_projection(self, enable: bool):
+        hfs_set_norm_projection(self.h, enable)
+
+    def set_dft_engine(self, engine: int):
+        hfs_set_dft_engine(self.h, engine)
 
     def set_time(self, t: float):
         hfs_set_time(self.h, t)

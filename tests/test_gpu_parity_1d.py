@@ -365,12 +365,12 @@ def test_norm_and_energy_match_oracle(precision):
     outs = [np.asarray(v, dtype=np.complex128) for v in s.split(s.get_psi())]
     nrm, en = s.norm(), s.energy()
     t = s.time
-    tol = 1e-12 if precision == "c128" else 2e-6
+    tol = 1e-12 if precision == "c128" else 1e-6
     for i, inst in enumerate(insts):
         p = O.Problem(**inst.as_dict())
         assert abs(nrm[i] - O.norm(p, outs[i])) <= tol * abs(nrm[i])
         assert abs(en[i] - O.energy(p, outs[i], t)) <= tol * 10 * max(1.0, abs(en[i]))
-        assert abs(nrm[i] - 1.0) < (1e-12 if precision == "c128" else 2e-6)  # norm conservation
+        assert abs(nrm[i] - 1.0) < (1e-12 if precision == "c128" else 1e-6)  # norm conservation
 
 
 def test_eigenstate_phase_gpu():
