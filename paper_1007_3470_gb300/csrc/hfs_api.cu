@@ -92,7 +92,7 @@ double omega_bound(const hfs_instance &p, double t0, double t1)
 namespace {
 
 struct Layout {
-    size_t status, ticket, tdev, inst, order, work, twf, twd, fge, nodes, rec, diag, norm, total;
+    size_t status, ticket, tdev, inst, order, work, twf, twd, twp, fge, nodes, rec, diag, norm, total;
 };
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -184,6 +184,7 @@ Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
     L.work = take(sizeof(WorkItem) * std::max<int64_t>(c->count, 1));
     L.twf = take(sizeof(float4) * kTwiddleTotal);
     L.twd = take(sizeof(cpx<double>) * kTwiddleTotal);
+    L.twp = take(sizeof(float2) * kTwiddleTotal);
     L.fge = take(sizeof(StageFGE) * c->count * nstage * c->dim);
     L.nodes = take(law_nodes_bytes(nstage));
     L.rec = take(recsz * c->count * (nstage + 1));
@@ -303,6 +304,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.ticket = ticket;
             a.status = status;
             a.norm_target = wptr<float>(c, c->lay.norm);
+            a.tw2 = wptr<void>(c, c->lay.twp);
             const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64, c->variant)));
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
             if (c->profiling && done == 0) CK(record_prof(c, 0));
@@ -533,6 +535,7 @@ int hfs_bind(hfs_ctx_t c, void *psi, void *work, size_t work_bytes, int64_t chun
         if (s) return s;
     }
     CK(launch_twiddles(wptr<void>(c, L.twf), wptr<void>(c, L.twd), c->stream));
+    CK(launch_twiddles_plain(wptr<void>(c, L.twp), c->stream));
     CK(launch_set_time(wptr<double>(c, L.tdev), c->t, c->stream));
     return HFS_OK;
 }

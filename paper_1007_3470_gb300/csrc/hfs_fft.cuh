@@ -199,7 +199,20 @@ template <typename R> struct TwOf;
 template <> struct TwOf<float> { using type = float4; };
 template <> struct TwOf<double> { using type = double2; };
 
+// Table element type: TWC (compensated) FP32 twiddles are (hi, lo) pairs;
+// without TWC a plain FP32 table (the rounded value only) serves kernels
+// whose norm is restored every sub-stage (the projected 1D step), where the
+// systematic norm bias of rounded twiddles does not accumulate.
+template <typename R, bool TWC> struct TwTab { using type = typename TwOf<R>::type; };
+template <> struct TwTab<float, false> { using type = float2; };
+
 // a * w (forward) or a * conj(w) (inverse), w = tw[i]
+template <bool INV> __device__ __forceinline__ cpx<float> tw_mul(cpx<float> a, const float2 *tw, int i)
+{
+    const float2 w = __ldg(tw + i);
+    return INV ? cpx<float>{fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -(a.x * w.y))}
+               : cpx<float>{fmaf(a.x, w.x, -(a.y * w.y)), fmaf(a.x, w.y, a.y * w.x)};
+}
 template <bool INV> __device__ __forceinline__ cpx<float> tw_mul(cpx<float> a, const float4 *tw, int i)
 {
     const float4 w = __ldg(tw + i);
@@ -253,9 +266,9 @@ template <int T, bool TEAM> __device__ __forceinline__ void exchange_sync(int ba
 }
 
 // One Stockham pass; see the layout contract at the top of the file.
-template <int N, int E, int RAD, int NS, bool INV, bool LAST, int ILV, bool TEAM, typename R>
+template <int N, int E, int RAD, int NS, bool INV, bool LAST, int ILV, bool TEAM, typename R, bool TWC = true>
 __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
-                                              const typename TwOf<R>::type *__restrict__ tw, int bar)
+                                              const typename TwTab<R, TWC>::type *__restrict__ tw, int bar)
 {
     constexpr int T = N / E;
     constexpr int Q = E / RAD;
@@ -263,7 +276,7 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
     // The twiddles of a thread are the same at every time step; without this
     // opaque copy of the table pointer the compiler hoists all of them out of
     // the time loop and keeps every pass's twiddles live in registers.
-    const typename TwOf<R>::type *twp = tw;
+    const typename TwTab<R, TWC>::type *twp = tw;
     asm volatile("" : "+l"(twp));
     // likewise the forward and inverse transforms compute identical integer
     // offsets; recomputing them per pass is cheaper than holding them live
@@ -301,23 +314,24 @@ __device__ __forceinline__ void stockham_pass(cpx<R> (&v)[E], cpx<R> *sm, int t,
     }
 }
 
-template <int N, int E, bool INV, int ILV, bool TEAM, typename R, int NS, int RAD, int... REST>
+template <int N, int E, bool INV, int ILV, bool TEAM, typename R, bool TWC, int NS, int RAD, int... REST>
 __device__ __forceinline__ void fft_passes(cpx<R> (&v)[E], cpx<R> *sm, int t,
-                                           const typename TwOf<R>::type *__restrict__ tw, int bar)
+                                           const typename TwTab<R, TWC>::type *__restrict__ tw, int bar)
 {
-    stockham_pass<N, E, RAD, NS, INV, sizeof...(REST) == 0, ILV, TEAM>(v, sm, t, tw, bar);
-    if constexpr (sizeof...(REST) > 0) fft_passes<N, E, INV, ILV, TEAM, R, NS * RAD, REST...>(v, sm, t, tw, bar);
+    stockham_pass<N, E, RAD, NS, INV, sizeof...(REST) == 0, ILV, TEAM, R, TWC>(v, sm, t, tw, bar);
+    if constexpr (sizeof...(REST) > 0)
+        fft_passes<N, E, INV, ILV, TEAM, R, TWC, NS * RAD, REST...>(v, sm, t, tw, bar);
 }
 
 // Radix sequences per (N, elements per thread).
 template <int N, int E> struct FftPlan;
 #define HFS_PLAN(NN, EE, ...)                                                                          \
     template <> struct FftPlan<NN, EE> {                                                                \
-        template <bool INV, typename R, int ILV = 1, bool TEAM = false>                                 \
+        template <bool INV, typename R, int ILV = 1, bool TEAM = false, bool TWC = true>                \
         static __device__ __forceinline__ void run(cpx<R> (&v)[EE], cpx<R> *sm, int t,                   \
-                                                   const typename TwOf<R>::type *tw, int bar = 0)       \
+                                                   const typename TwTab<R, TWC>::type *tw, int bar = 0) \
         {                                                                                               \
-            fft_passes<NN, EE, INV, ILV, TEAM, R, 1, __VA_ARGS__>(v, sm, t, tw, bar);                   \
+            fft_passes<NN, EE, INV, ILV, TEAM, R, TWC, 1, __VA_ARGS__>(v, sm, t, tw, bar);              \
         }                                                                                               \
     };
 HFS_PLAN(4096, 16, 16, 16, 16)

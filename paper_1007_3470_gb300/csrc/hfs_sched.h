@@ -60,6 +60,7 @@ struct Step1DArgs {
     const void *tw;                 // twiddle table (cpx<R>)
     unsigned *ticket;
     unsigned *status;
+    const void *tw2;                // plain FP32 twiddle table (float2), read with the norm projection
     float *norm_target;             // per instance: target sum |u|^2 of the norm projection
     int32_t proj;                   // PROJ_OFF, PROJ_SET (first launch of a call), PROJ_USE
 };
@@ -85,6 +86,8 @@ struct Diag1DArgs {
 cudaError_t launch_diag1d(bool fp64, const Diag1DArgs &a, int grid, cudaStream_t st);
 
 cudaError_t launch_twiddles(void *tw_f, void *tw_d, cudaStream_t st);
+// the plain FP32 table (same layout, the FP64 value rounded to float2)
+cudaError_t launch_twiddles_plain(void *tw_p, cudaStream_t st);
 
 // host helpers shared by the entry points (hfs_api.cu)
 int composition_fixed(int comp, double *a, double *b, int *m);

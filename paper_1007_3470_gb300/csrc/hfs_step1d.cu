@@ -111,6 +111,22 @@ __global__ void twiddle_kernel(float4 *tf, double2 *td)
     tf[i] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(-sn - (double)sh));
 }
 
+__global__ void twiddle_plain_kernel(float2 *tp)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= kTwiddleTotal) return;
+    int L = 4;
+    while (i >= tw_pass_offset(2 * L, 2)) L <<= 1;
+    int R = 2;
+    while (R < 16 && i >= tw_pass_offset(L, 2 * R)) R <<= 1;
+    const int64_t s = i - tw_pass_offset(L, R);
+    const int NS = L / R;
+    const int64_t r = s / NS + 1, j = s % NS;
+    double sn, cs;
+    sincospi(2.0 * (double)(j * r) / (double)L, &sn, &cs);
+    tp[i] = make_float2((float)cs, (float)-sn);
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -176,6 +192,12 @@ cudaError_t launch_diag1d(bool fp64, const Diag1DArgs &a, int grid, cudaStream_t
     const size_t bytes = step1d_smem_bytes(fp64);
     if (fp64) diag1d_kernel<double><<<grid, kCtaThreads, bytes, st>>>(a);
     else diag1d_kernel<float><<<grid, kCtaThreads, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles_plain(void *tw_p, cudaStream_t st)
+{
+    twiddle_plain_kernel<<<(unsigned)((kTwiddleTotal + 255) / 256), 256, 0, st>>>((float2 *)tw_p);
     return cudaGetLastError();
 }
 

@@ -225,6 +225,18 @@ template <int T> __device__ __forceinline__ float team_sum_end(float s, const fl
     }
 }
 
+// The transforms of the step: with the norm projection (FP32) the plain
+// twiddle table, otherwise the compensated one.
+template <bool INV, bool PROJ, int N, int E, typename R>
+__device__ __forceinline__ void fft(const Step1DArgs &a, cpx<R> (&v)[E], cpx<R> *sm, int t,
+                                    const typename TwOf<R>::type *tw, int g)
+{
+    if constexpr (PROJ && sizeof(R) == 4)
+        FftPlan<N, E>::template run<INV, R, 1, HFS_TEAM_SYNC, false>(v, sm, t, static_cast<const float2 *>(a.tw2),
+                                                                     1 + g);
+    else FftPlan<N, E>::template run<INV, R, 1, HFS_TEAM_SYNC>(v, sm, t, tw, 1 + g);
+}
+
 // sub-stages [j0, j1): X_j, forward FFT, kinetic phase (+ projection), inverse FFT
 template <typename R, int VI, int N, int E, bool PROJ, typename Rec>
 __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], int t, int g, bool active, int idx,
@@ -248,7 +260,7 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
         float dsum = 0.0f;
         xphase<N, E, VI>(v, tl, rc, tp, vt, dsum);
         if constexpr (PROJ) dsum = team_sum_begin<T>(dsum, slots);
-        FftPlan<N, E>::template run<false, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
+        fft<false, PROJ, N>(a, v, sm, tl, tw, g);
         float C = 1.0f;
         if constexpr (PROJ) {
             const float s = team_sum_end<T>(dsum, slots, g);
@@ -260,7 +272,7 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
             }
         }
         kphase<N, E, PROJ>(v, tl, rc, C);
-        FftPlan<N, E>::template run<true, R, 1, HFS_TEAM_SYNC>(v, sm, tl, tw, 1 + g);
+        fft<true, PROJ, N>(a, v, sm, tl, tw, g);
     }
 }
 
