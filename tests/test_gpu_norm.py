@@ -97,3 +97,25 @@ def test_projection_off_is_the_default_and_unsupported_elsewhere():
             s.set_norm_projection(True)
         assert ei.value.code == 2  # HFS_ERR_UNSUPPORTED
         s.close()
+
+
+@pytest.mark.parametrize("scheme,h", [("ni5_84", 0.01), ("srkn6_4", 0.01), ("strang", 0.005)])
+def test_time_dependent_gpe_full_length_with_projection(scheme, h):
+    """The time-dependent GPE (N = 1024, omega = 1 + 0.5 sin 2t, sigma = 10,
+    T = 10) with the projection: within the parity bound of the oracle and
+    within 1e-6 of the initial norm after 1000-2000 steps."""
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    inst, psi0, steps = W.gpe_tdep_1d(h=h, scheme=scheme)
+    ref = O.run(O.Problem(**inst.as_dict()), psi0, steps)
+    s = hfs.Solver([inst], precision="c64", chunk_steps=steps)
+    s.set_schedule(h, scheme, hfs.HFS_FLOW_CF4)
+    s.set_norm_projection(True)
+    s.set_psi([psi0])
+    n0 = s.norm()[0]
+    s.step(steps)
+    out = s.get_psi()
+    n1 = s.norm()[0]
+    s.close()
+    assert O.rel_l2(out, ref) <= budget(TOL_C64, steps * h)
+    assert abs(n1 / n0 - 1.0) <= DRIFT
