@@ -223,6 +223,7 @@ def extra_measurements(hfs, W, torch):
     insts, psis, _ = W.batch_1d(count=COUNT, h=DT, steps=STEPS)
     ss = hfs.Solver(insts, precision="c64", chunk_steps=STEPS)
     ss.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    ss.set_norm_projection(True)
     ss.set_mode(hfs.HFS_MODE_STREAMING, 1)
     ss.autotune(trial_steps=2)
     ss.set_graphs(True)
@@ -247,8 +248,38 @@ def extra_measurements(hfs, W, torch):
     msb = kernel_ms(sb, 200)
     sb.close()
     out["n256_T1_single_vs_batch"] = {"single_solves_per_s": 1e3 / ms1, "batch4096_solves_per_s": 4096e3 / msb}
+    out["ho_vs_f_split"] = split_comparison(hfs, W)
     out["batch65536_streaming_hbm"] = hbm_streaming_measurement(hfs, W)
     out["surrogate_fno"] = surrogate_measurement()
+    return out
+
+
+def split_comparison(hfs, W):
+    """HO split vs F split at equal FFT count (Sec. 4): the leap-frog BAB
+    composition with both splittings on the autonomous problem mu = omega = 1,
+    V_I = 0, psi0 = rho exp(-(x-1)^2/2), N = 1024, T = 10, in FP64 on the GPU;
+    relative L2 error against the oracle's NI_5(8,4) HO-split solution at
+    dt = 0.001.  FFT pairs per solve = T / dt for both splits."""
+    from oracle import oracle as O
+    T, out = 10.0, {}
+    for sigma, dts in ((0.01, (0.04, 0.02, 0.01, 0.005)), (1.0, (0.04, 0.02, 0.01, 0.005)),
+                       (100.0, (0.01, 0.005, 0.0025))):
+        ref_inst, psi0 = W.split_comparison_1d(sigma, h=0.001)
+        ref_inst.scheme = "ni5_84"
+        ref = O.run(O.Problem(**ref_inst.as_dict()), psi0, int(round(T / 0.001)))
+        rows = []
+        for h in dts:
+            row = {"dt": h, "fft_pairs": int(round(T / h))}
+            for split, name in ((W.SPLIT_HO, "ho"), (W.SPLIT_FOURIER, "f")):
+                inst, _ = W.split_comparison_1d(sigma, h=h, split=split)
+                s = hfs.Solver([inst], precision="c128", chunk_steps=512)
+                s.set_schedule(h, "strang", hfs.HFS_FLOW_LEMMA2, split=split)
+                s.set_psi([psi0])
+                s.step(int(round(T / h)))
+                row["err_" + name] = O.rel_l2(s.get_psi(), ref)
+                s.close()
+            rows.append(row)
+        out[f"sigma_{sigma:g}"] = rows
     return out
 
 
@@ -297,6 +328,7 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
     pts = sum(i.n[0] for i in insts)
     s = hfs.Solver(insts, precision="c64", chunk_steps=steps)
     s.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
+    s.set_norm_projection(True)
     s.set_mode(hfs.HFS_MODE_STREAMING, 1)
     # plans per grid size measured in this mode (2 trial steps: 44 step launches)
     tuned = s.autotune(trial_steps=2)

@@ -111,6 +111,16 @@ def gpe_tdep_1d(h: float = 0.01, n: int = 1024, T: float = 10.0, scheme: str = "
     return inst, gaussian_1d(inst), steps
 
 
+def split_comparison_1d(sigma: float, n: int = 1024, h: float = 0.01, split: int = SPLIT_HO):
+    """The HO-split vs F-split experiment of Sec. 4: mu = omega = 1, V_I = 0,
+    psi0 = rho exp(-(x-1)^2/2), x in [-20,20) for sigma = 0.01 and [-30,30)
+    otherwise (the paper's intervals), leap-frog BAB composition."""
+    half = 20.0 if sigma < 0.1 else 30.0
+    inst = Instance(n=[n], a=[-half], b=[half], omega_law=OMEGA_CONST, w0=1.0, sigma=sigma,
+                    split=split, ho_flow=FLOW_LEMMA2, scheme="strang", h=h)
+    return inst, gaussian_1d(inst, x0=1.0)
+
+
 # ---------------------------------------------------------------------------
 # batched 1D workload
 # ---------------------------------------------------------------------------

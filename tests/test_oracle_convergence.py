@@ -56,3 +56,21 @@ def test_p8_exact_flow_constant_omega_any_h():
     u1 = O.run(make(0.8), psi0, 5)
     u2 = O.run(make(0.4), psi0, 10)
     assert O.rel_l2(u1, u2) < 1e-13
+
+
+@pytest.mark.parametrize("sigma,factor", [(0.01, 100.0), (1.0, 2.0)])
+def test_ho_split_beats_f_split_at_equal_fft_count(sigma, factor):
+    """Sec. 4 (HO-split versus F-split): with the same leap-frog composition,
+    hence the same number of FFTs per step, the HO split is the more accurate
+    one for a weakly perturbed oscillator (sigma = 0.01, 1); the reference is
+    the fourth-order NI_5(8,4) HO split at a much smaller step."""
+    T = 2.0
+    ref_inst, psi0 = W.split_comparison_1d(sigma, n=512, h=0.002)
+    ref_inst.scheme = "ni5_84"
+    ref = O.run(O.Problem(**ref_inst.as_dict()), psi0, int(round(T / 0.002)))
+    for h in (0.04, 0.02):
+        errs = {}
+        for split in (O.SPLIT_HO, O.SPLIT_FOURIER):
+            inst, _ = W.split_comparison_1d(sigma, n=512, h=h, split=split)
+            errs[split] = O.rel_l2(O.run(O.Problem(**inst.as_dict()), psi0, int(round(T / h))), ref)
+        assert errs[O.SPLIT_HO] * factor < errs[O.SPLIT_FOURIER], (h, errs)
