@@ -222,16 +222,40 @@ int hfs_sync_status(hfs_ctx_t ctx);
 
 /* ---- plans / autotuning (1D) ------------------------------------------- */
 
-/* Set the plan for grid size n: elements per thread (8 or 16).  Affects
- * later hfs_step calls.  Errors: HFS_ERR_UNSUPPORTED. */
-int hfs_set_plan(hfs_ctx_t ctx, int n, int elems_per_thread);
+/* Plan of the grid size n: plan = elements per thread (16, 8 for n <= 2048,
+ * 4 for n <= 1024), | HFS_PLAN_ALT_ORDER for the alternative order of the
+ * Stockham radices with 16 values per thread (radix 8 throughout at n = 4096,
+ * the small radix first otherwise).  4 values per thread and the alternative
+ * order are complex64 only.  Affects later hfs_step calls.
+ * Errors: HFS_ERR_UNSUPPORTED. */
+#define HFS_PLAN_ALT_ORDER 0x100
+int hfs_set_plan(hfs_ctx_t ctx, int n, int plan);
 
-/* Time each supported plan for each grid size present in the batch with
- * CUDA events (trial_steps steps, resident mode) and keep the fastest.
- * Overwrites the state: call before hfs_set_psi.  best_ept[6] (host, may be
- * NULL) receives the chosen elements-per-thread for n = 128 ... 4096 (0 when
- * the size is absent). */
-int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_ept);
+/* CTAs per SM of the persistent 1D step grid (0: as many as fit, the
+ * default; values above that are clamped). */
+int hfs_set_occupancy(hfs_ctx_t ctx, int ctas_per_sm);
+
+/* Search the 1D plans with CUDA-event timings of trial_steps steps each in
+ * the current mode (resident or streaming) and keep the fastest: per grid
+ * size present, every admissible plan (16, 8, 4 values per thread, the
+ * alternative radix order) on that size's work items alone; then the whole
+ * batch with the chosen plans against the default kernel's plans (a wide
+ * plan moves the launch to the larger wide kernel) and one CTA per SM
+ * against as many as fit.  Overwrites the state: call before hfs_set_psi.
+ * best_plans[6] (host, may be NULL) receives the chosen plan (as for
+ * hfs_set_plan) for n = 128 ... 4096, 0 where the size is absent. */
+int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_plans);
+
+/* hfs_autotune with a persistent cache: the JSON file at `path` holds tuned
+ * plans keyed by the GPU name and SM count, the precision, a hash of the
+ * library's sources, the perturbation-kind variant, the norm projection, the
+ * mode, the schedule (flow, split, stages) and the batch's count of
+ * instances per grid size.  A matching entry is applied without timing
+ * anything (*hit = 1); otherwise the search runs and its result is added to
+ * the file (*hit = 0; the file is written to path.tmp and renamed).
+ * Errors: as hfs_autotune; HFS_ERR_INVALID_ARG when the file cannot be
+ * written. */
+int hfs_autotune_cache(hfs_ctx_t ctx, const char *path, int trial_steps, int32_t *best_plans, int *hit);
 
 /* ---- profiling -------------------------------------------------------- */
 

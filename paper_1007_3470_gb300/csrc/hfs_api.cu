@@ -4,10 +4,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
 #include <map>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -106,8 +109,12 @@ struct hfs_ctx_s {
     std::vector<DevInst> dinst;
     std::vector<int64_t> offsets;
     int64_t elems = 0;
-    // 1D plans: elements per thread per size class
+    // 1D plans per size class: elements per thread (4, 8, 16) and the
+    // alternative radix order (16 only); CTAs per SM of the step grid (0: as
+    // many as fit)
     int ept[kNumSizes] = {16, 16, 16, 16, 16, 16};
+    bool alt[kNumSizes] = {false, false, false, false, false, false};
+    int ctas_per_sm = 0;
     // trap law shared by every instance (HFS_OMEGA_*), -1 for a mixed batch,
     // and whether its parameters are shared too
     int law = -1;
@@ -207,13 +214,14 @@ void build_worklist(hfs_ctx_s *c)
     while (i < c->count) {
         const int n = c->inst[c->order[i]].n[0];
         const int e = c->ept[size_class(n)];
+        const bool alt = c->alt[size_class(n)];
         const int per = kCtaThreads / (n / e);
         int64_t j = i;
         while (j < c->count && j - i < per && c->inst[c->order[j]].n[0] == n) ++j;
         WorkItem w;
         w.first = (int32_t)i;
         w.count = (int32_t)(j - i);
-        w.plan = plan_id(n, e);
+        w.plan = plan_id(n, e, alt);
         w.pad = 0;
         c->work.push_back(w);
         i = j;
@@ -270,6 +278,24 @@ int check_validity(const hfs_ctx_s *c, int64_t nsteps)
     return HFS_OK;
 }
 
+// the work list holds a plan of the wide set
+bool worklist_wide(const hfs_ctx_s *c)
+{
+    for (const WorkItem &w : c->work)
+        if (plan_is_wide(w.plan)) return true;
+    return false;
+}
+
+// persistent grid of the 1D step: CTAs per SM (the tuned value, else as many
+// as fit) times the SMs, at most one CTA per work item
+int step_grid(const hfs_ctx_s *c, bool wide)
+{
+    const bool fp64 = c->precision == HFS_C128;
+    const int fit = step1d_ctas_per_sm(fp64, c->variant, wide);
+    const int per_sm = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, fit) : fit;
+    return std::max(1, std::min<int>((int)c->work.size(), c->sm_count * per_sm));
+}
+
 // enqueue nsteps steps (no graph logic); work list already uploaded
 int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
 {
@@ -305,7 +331,8 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.status = status;
             a.norm_target = wptr<float>(c, c->lay.norm);
             a.tw2 = wptr<void>(c, c->lay.twp);
-            const int grid = std::max(1, std::min<int>(a.nwork, c->sm_count * step1d_ctas_per_sm(fp64, c->variant)));
+            const bool wide = worklist_wide(c);
+            const int grid = step_grid(c, wide);
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
             if (c->profiling && done == 0) CK(record_prof(c, 0));
             for (int64_t s0 = 0; s0 < S; s0 += per) {
@@ -316,7 +343,7 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
                 // the first launch of the call records the norm it projects onto
                 a.proj = !c->norm_projection ? PROJ_OFF : (done == 0 && s0 == 0) ? PROJ_SET : PROJ_USE;
                 CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
-                CK(launch_step1d(fp64, c->variant, a, grid, c->stream));
+                CK(launch_step1d(fp64, c->variant, a, grid, c->stream, wide));
             }
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
         } else {
@@ -773,87 +800,319 @@ int hfs_sync_status(hfs_ctx_t c)
     return HFS_OK;
 }
 
-int hfs_set_plan(hfs_ctx_t c, int n, int ept)
+int hfs_set_plan(hfs_ctx_t c, int n, int plan)
 {
     if (!c || c->dim != 1) return HFS_ERR_INVALID_ARG;
     const int sc = size_class(n);
-    if (sc < 0 || (ept != 16 && ept != 8) || (ept == 8 && n > 2048)) return HFS_ERR_UNSUPPORTED;
+    const int ept = plan & 0xff;
+    const bool alt = (plan & HFS_PLAN_ALT_ORDER) != 0;
+    if (sc < 0 || (plan & ~(0xff | HFS_PLAN_ALT_ORDER))) return HFS_ERR_UNSUPPORTED;
+    if (ept != 16 && ept != 8 && ept != 4) return HFS_ERR_UNSUPPORTED;
+    if ((ept == 8 && n > 2048) || (ept == 4 && n > 1024) || (alt && ept != 16)) return HFS_ERR_UNSUPPORTED;
+    // the wide plans (four values per thread, alternative orders) are FP32 only
+    if ((ept == 4 || alt) && c->precision != HFS_C64) return HFS_ERR_UNSUPPORTED;
     c->ept[sc] = ept;
+    c->alt[sc] = alt;
     build_worklist(c);
     drop_graphs(c);
     if (c->work_base) return upload_tables(c);
     return HFS_OK;
 }
 
-int hfs_autotune(hfs_ctx_t c, int trial_steps, int32_t *best_ept)
+int hfs_set_occupancy(hfs_ctx_t c, int ctas_per_sm)
+{
+    if (!c || c->dim != 1 || ctas_per_sm < 0) return HFS_ERR_INVALID_ARG;
+    c->ctas_per_sm = ctas_per_sm;
+    drop_graphs(c);
+    return HFS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int encode_plan(const hfs_ctx_s *c, int k) { return c->ept[k] | (c->alt[k] ? HFS_PLAN_ALT_ORDER : 0); }
+
+// time `steps` steps of the current work list (resident or streaming as
+// set); the first of two runs warms up
+int time_worklist(hfs_ctx_s *c, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    int s = upload_tables(c);
+    if (s) return s;
+    for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, c->stream));
+        s = enqueue_steps(c, steps);
+        if (s) return s;
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+    }
+    return HFS_OK;
+}
+
+// The search of hfs_autotune (see include/hfs.h).
+int autotune(hfs_ctx_s *c, int trial_steps, float *best_total)
+{
+    const int64_t steps = std::min<int64_t>(trial_steps, c->chunk);
+    bool present[kNumSizes] = {};
+    for (auto &p : c->inst) present[size_class(p.n[0])] = true;
+    // a smooth (zero) state keeps every trial well defined
+    size_t bytes = 0;
+    hfs_state_size(c, nullptr, &bytes);
+    CK(cudaMemsetAsync(c->psi, 0, bytes, c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const bool fp32 = c->precision == HFS_C64;
+    int s = HFS_OK;
+    // 1. per size class, each plan timed on that class's work items alone
+    const int cand[4] = {16, 8, 16 | HFS_PLAN_ALT_ORDER, 4};
+    for (int k = 0; k < kNumSizes && !s; ++k) {
+        if (!present[k]) continue;
+        const int n = 128 << k;
+        float best = INFINITY;
+        int best_plan = encode_plan(c, k);
+        for (int ci = 0; ci < 4 && !s; ++ci) {
+            const int plan = cand[ci], ept = plan & 0xff;
+            const bool alt = (plan & HFS_PLAN_ALT_ORDER) != 0;
+            if ((ept == 8 && n > 2048) || (ept == 4 && n > 1024)) continue;
+            if ((ept == 4 || alt) && !fp32) continue;
+            c->ept[k] = ept;
+            c->alt[k] = alt;
+            build_worklist(c);
+            std::vector<WorkItem> keep;
+            for (auto &w : c->work)
+                if (w.plan == plan_id(n, ept, alt)) keep.push_back(w);
+            c->work.swap(keep);
+            float ms = 0.0f;
+            s = time_worklist(c, steps, e0, e1, &ms);
+            if (!s && ms < best) {
+                best = ms;
+                best_plan = plan;
+            }
+        }
+        c->ept[k] = best_plan & 0xff;
+        c->alt[k] = (best_plan & HFS_PLAN_ALT_ORDER) != 0;
+    }
+    // 2. the whole batch: the chosen plans against the best of the default
+    //    kernel's plans alone (a wide plan anywhere moves the whole launch to
+    //    the wide kernel), then 1 CTA per SM against as many as fit
+    float total = INFINITY;
+    if (!s) {
+        build_worklist(c);
+        s = time_worklist(c, steps, e0, e1, &total);
+    }
+    if (!s && worklist_wide(c)) {
+        int save_e[kNumSizes];
+        bool save_a[kNumSizes];
+        std::copy(c->ept, c->ept + kNumSizes, save_e);
+        std::copy(c->alt, c->alt + kNumSizes, save_a);
+        // best default-kernel plan per class: the chosen one if it is not
+        // wide, else 16 values per thread
+        for (int k = 0; k < kNumSizes; ++k)
+            if (c->alt[k] || c->ept[k] == 4) {
+                c->ept[k] = 16;
+                c->alt[k] = false;
+            }
+        build_worklist(c);
+        float ms = 0.0f;
+        s = time_worklist(c, steps, e0, e1, &ms);
+        if (!s && ms < total) {
+            total = ms;
+        } else {
+            std::copy(save_e, save_e + kNumSizes, c->ept);
+            std::copy(save_a, save_a + kNumSizes, c->alt);
+        }
+    }
+    if (!s) {
+        // one CTA per SM against the current setting (as many as fit)
+        build_worklist(c);
+        const int keep = c->ctas_per_sm;
+        c->ctas_per_sm = 1;
+        float ms = 0.0f;
+        s = time_worklist(c, steps, e0, e1, &ms);
+        if (!s && ms < total) total = ms;
+        else c->ctas_per_sm = keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_total) *best_total = total;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hfs_autotune(hfs_ctx_t c, int trial_steps, int32_t *best_plans)
 {
     NvtxRange nvtx_range("hfs_autotune");
     int s = ready(c);
     if (s) return s;
     if (!c->have_sched || c->dim != 1 || trial_steps < 1) return HFS_ERR_INVALID_ARG;
-    const int64_t steps = std::min<int64_t>(trial_steps, c->chunk);
-    std::vector<hfs_instance> all = c->inst;
-    bool present[kNumSizes] = {};
-    for (auto &p : all) present[size_class(p.n[0])] = true;
-    // fill psi with a smooth constant so that the trial is well defined
-    size_t bytes = 0;
-    hfs_state_size(c, nullptr, &bytes);
-    CK(cudaMemsetAsync(c->psi, 0, bytes, c->stream));
     const bool graphs = c->graphs;
     c->graphs = false;
     const double t_save = c->t;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    const int options[2] = {16, 8};
-    for (int k = 0; k < kNumSizes; ++k) {
-        if (!present[k]) {
-            if (best_ept) best_ept[k] = 0;
-            continue;
-        }
-        const int n = 128 << k;
-        float best = INFINITY;
-        int best_e = c->ept[k];
-        for (int oi = 0; oi < 2; ++oi) {
-            const int e = options[oi];
-            if (e == 8 && n > 2048) continue;
-            // restrict the work list to this size class
-            c->ept[k] = e;
-            build_worklist(c);
-            std::vector<WorkItem> keep;
-            for (auto &w : c->work)
-                if (w.plan == plan_id(n, e)) keep.push_back(w);
-            c->work.swap(keep);
-            s = upload_tables(c);
-            if (s) break;
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {  // first run warms up
-                CK(cudaEventRecord(e0, c->stream));
-                s = enqueue_steps(c, steps);
-                if (s) break;
-                CK(cudaEventRecord(e1, c->stream));
-                CK(cudaEventSynchronize(e1));
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-            }
-            if (s) break;
-            if (ms < best) {
-                best = ms;
-                best_e = e;
-            }
-        }
-        if (s) break;
-        c->ept[k] = best_e;
-        if (best_ept) best_ept[k] = best_e;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    s = autotune(c, trial_steps, nullptr);
     c->graphs = graphs;
     build_worklist(c);
     int s2 = upload_tables(c);
     c->t = t_save;
     if (c->work_base) CK(launch_set_time(wptr<double>(c, c->lay.tdev), t_save, c->stream));
     drop_graphs(c);
+    if (best_plans) {
+        bool present[kNumSizes] = {};
+        for (auto &p : c->inst) present[size_class(p.n[0])] = true;
+        for (int k = 0; k < kNumSizes; ++k) best_plans[k] = present[k] ? encode_plan(c, k) : 0;
+    }
     return s ? s : s2;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// tuned-plan cache (a small JSON file; see hfs_autotune_cache in hfs.h)
+// ---------------------------------------------------------------------------
+namespace {
+
+#ifndef HFS_SOURCE_HASH
+#define HFS_SOURCE_HASH "unknown"
+#endif
+
+std::string cache_key(const hfs_ctx_s *c)
+{
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+    int count[kNumSizes] = {};
+    for (auto &p : c->inst) count[size_class(p.n[0])]++;
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|sm%d|%s|src=%s|vi=%d|proj=%d|mode=%d/%d|flow=%d|split=%d|m=%d|n=%d,%d,%d,%d,%d,%d",
+             prop.name, prop.multiProcessorCount, c->precision == HFS_C128 ? "c128" : "c64", HFS_SOURCE_HASH,
+             c->variant, c->norm_projection ? 1 : 0, c->mode, c->mode == HFS_MODE_STREAMING ? c->spl : 0,
+             c->sc.flow, c->sc.split, c->sc.m, count[0], count[1], count[2], count[3], count[4], count[5]);
+    std::string k(buf);
+    for (char &ch : k)
+        if (ch == '"' || ch == '\\') ch = '_';
+    return k;
+}
+
+struct CacheEntry {
+    std::string key;
+    int plans[kNumSizes];
+    int ctas_per_sm;
+    double ms;
+};
+
+bool read_file(const char *path, std::string &out)
+{
+    FILE *f = fopen(path, "rb");
+    if (!f) return false;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) out.append(buf, n);
+    fclose(f);
+    return true;
+}
+
+// entries of a cache file written by write_cache (one entry per line)
+std::vector<CacheEntry> parse_cache(const std::string &text)
+{
+    std::vector<CacheEntry> v;
+    size_t pos = 0;
+    const std::string kk = "\"key\": \"";
+    while ((pos = text.find(kk, pos)) != std::string::npos) {
+        pos += kk.size();
+        const size_t end = text.find('"', pos);
+        if (end == std::string::npos) break;
+        CacheEntry e{};
+        e.key = text.substr(pos, end - pos);
+        const size_t pl = text.find("\"plans\": [", end);
+        const size_t nl = text.find('\n', end);
+        if (pl == std::string::npos || (nl != std::string::npos && pl > nl)) continue;
+        if (sscanf(text.c_str() + pl, "\"plans\": [%d, %d, %d, %d, %d, %d], \"ctas_per_sm\": %d, \"ms\": %lf",
+                   &e.plans[0], &e.plans[1], &e.plans[2], &e.plans[3], &e.plans[4], &e.plans[5], &e.ctas_per_sm,
+                   &e.ms) == 8)
+            v.push_back(e);
+        pos = end;
+    }
+    return v;
+}
+
+bool write_cache(const char *path, const std::vector<CacheEntry> &v)
+{
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return false;
+    fprintf(f, "{\"hfs_tuned_plans\": 1, \"entries\": [\n");
+    for (size_t i = 0; i < v.size(); ++i) {
+        const CacheEntry &e = v[i];
+        fprintf(f, "  {\"key\": \"%s\", \"plans\": [%d, %d, %d, %d, %d, %d], \"ctas_per_sm\": %d, \"ms\": %.4f}%s\n",
+                e.key.c_str(), e.plans[0], e.plans[1], e.plans[2], e.plans[3], e.plans[4], e.plans[5], e.ctas_per_sm,
+                e.ms, i + 1 < v.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hfs_autotune_cache(hfs_ctx_t c, const char *path, int trial_steps, int32_t *best_plans, int *hit)
+{
+    int s = ready(c);
+    if (s) return s;
+    if (!path || !c->have_sched || c->dim != 1 || trial_steps < 1) return HFS_ERR_INVALID_ARG;
+    const std::string key = cache_key(c);
+    if (key.empty()) return HFS_ERR_CUDA;
+    std::string text;
+    std::vector<CacheEntry> entries;
+    if (read_file(path, text)) entries = parse_cache(text);
+    for (const CacheEntry &e : entries) {
+        if (e.key != key) continue;
+        for (int k = 0; k < kNumSizes; ++k) {
+            if (!e.plans[k]) continue;
+            s = hfs_set_plan(c, 128 << k, e.plans[k]);
+            if (s) return s;
+        }
+        c->ctas_per_sm = e.ctas_per_sm;
+        drop_graphs(c);
+        if (best_plans) std::copy(e.plans, e.plans + kNumSizes, best_plans);
+        if (hit) *hit = 1;
+        return HFS_OK;
+    }
+    const bool graphs = c->graphs;
+    c->graphs = false;
+    const double t_save = c->t;
+    float total = 0.0f;
+    s = autotune(c, trial_steps, &total);
+    c->graphs = graphs;
+    build_worklist(c);
+    int s2 = upload_tables(c);
+    c->t = t_save;
+    if (c->work_base) CK(launch_set_time(wptr<double>(c, c->lay.tdev), t_save, c->stream));
+    drop_graphs(c);
+    if (s || s2) return s ? s : s2;
+    CacheEntry e{};
+    e.key = key;
+    bool present[kNumSizes] = {};
+    for (auto &p : c->inst) present[size_class(p.n[0])] = true;
+    for (int k = 0; k < kNumSizes; ++k) e.plans[k] = present[k] ? encode_plan(c, k) : 0;
+    e.ctas_per_sm = c->ctas_per_sm;
+    e.ms = total;
+    bool replaced = false;
+    for (CacheEntry &o : entries)
+        if (o.key == key) {
+            o = e;
+            replaced = true;
+        }
+    if (!replaced) entries.push_back(e);
+    if (!write_cache(path, entries)) return HFS_ERR_INVALID_ARG;
+    if (best_plans) std::copy(e.plans, e.plans + kNumSizes, best_plans);
+    if (hit) *hit = 0;
+    return HFS_OK;
 }
 
 }  // extern "C"

@@ -323,10 +323,11 @@ __device__ __forceinline__ void fft_passes(cpx<R> (&v)[E], cpx<R> *sm, int t,
         fft_passes<N, E, INV, ILV, TEAM, R, TWC, NS * RAD, REST...>(v, sm, t, tw, bar);
 }
 
-// Radix sequences per (N, elements per thread).
-template <int N, int E> struct FftPlan;
-#define HFS_PLAN(NN, EE, ...)                                                                          \
-    template <> struct FftPlan<NN, EE> {                                                                \
+// Radix sequences per (N, elements per thread, ALT: the alternative order).
+template <int N, int E, bool ALT = false> struct FftPlan;
+#define HFS_PLAN(NN, EE, ...) HFS_PLAN_ORDER(NN, EE, false, __VA_ARGS__)
+#define HFS_PLAN_ORDER(NN, EE, AA, ...)                                                                \
+    template <> struct FftPlan<NN, EE, AA> {                                                            \
         template <bool INV, typename R, int ILV = 1, bool TEAM = false, bool TWC = true>                \
         static __device__ __forceinline__ void run(cpx<R> (&v)[EE], cpx<R> *sm, int t,                   \
                                                    const typename TwTab<R, TWC>::type *tw, int bar = 0) \
@@ -350,6 +351,19 @@ HFS_PLAN(512, 8, 8, 8, 8)
 HFS_PLAN(256, 8, 8, 8, 4)
 HFS_PLAN(128, 8, 8, 8, 2)
 HFS_PLAN(64, 8, 8, 8)
+// four values per thread (n <= 1024: at most 256 threads per instance)
+HFS_PLAN(1024, 4, 4, 4, 4, 4, 4)
+HFS_PLAN(512, 4, 4, 4, 4, 4, 2)
+HFS_PLAN(256, 4, 4, 4, 4, 4)
+HFS_PLAN(128, 4, 4, 4, 4, 2)
+// sixteen values per thread, alternative radix orders
+HFS_PLAN_ORDER(4096, 16, true, 8, 8, 8, 8)
+HFS_PLAN_ORDER(2048, 16, true, 8, 16, 16)
+HFS_PLAN_ORDER(1024, 16, true, 4, 16, 16)
+HFS_PLAN_ORDER(512, 16, true, 2, 16, 16)
+HFS_PLAN_ORDER(256, 16, true, 4, 4, 16)
+HFS_PLAN_ORDER(128, 16, true, 8, 16)
 #undef HFS_PLAN
+#undef HFS_PLAN_ORDER
 
 }  // namespace hfs

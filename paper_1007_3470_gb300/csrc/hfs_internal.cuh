@@ -116,8 +116,16 @@ __host__ __device__ constexpr int size_class(int n)
 {
     return n == 128 ? 0 : n == 256 ? 1 : n == 512 ? 2 : n == 1024 ? 3 : n == 2048 ? 4 : n == 4096 ? 5 : -1;
 }
-// plan id = size_class * 2 + (ept == 8 ? 1 : 0)
-__host__ __device__ constexpr int plan_id(int n, int ept) { return size_class(n) * 2 + (ept == 8 ? 1 : 0); }
+// 1D plans: E values per thread and the order of the Stockham radices.
+// plan code 0: E = 16, radix-16 passes first; 1: E = 8 (radix 8); 2: E = 16,
+// the alternative order (radix 8 throughout for n = 4096, the small radix
+// first otherwise); 3: E = 4 (radix 4).  plan id = size_class * 4 + code.
+constexpr int kPlanCodes = 4;
+__host__ __device__ constexpr int plan_code(int ept, bool alt) { return ept == 16 ? (alt ? 2 : 0) : ept == 8 ? 1 : 3; }
+__host__ __device__ constexpr int plan_id(int n, int ept, bool alt = false) { return size_class(n) * kPlanCodes + plan_code(ept, alt); }
+// codes 2 and 3 live in the "wide" step kernels only (the default kernels
+// keep the smaller instruction footprint)
+__host__ __device__ constexpr bool plan_is_wide(int plan) { return (plan % kPlanCodes) >= 2; }
 
 constexpr int kCtaThreads = 256;
 

@@ -6,16 +6,20 @@
 
 namespace hfs {
 
-HFS_STEP1D_VARIANT(, float, -1)
-HFS_STEP1D_VARIANT(, double, -1)
-HFS_STEP1D_VARIANT(extern, float, HFS_VI_NONE)
-HFS_STEP1D_VARIANT(extern, float, HFS_VI_X4)
-HFS_STEP1D_VARIANT(extern, float, HFS_VI_COS)
+HFS_STEP1D_VARIANT(, float, -1, false)
+HFS_STEP1D_VARIANT(, double, -1, false)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_NONE, false)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_X4, false)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_COS, false)
+HFS_STEP1D_VARIANT(extern, float, -1, true)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_NONE, true)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_X4, true)
+HFS_STEP1D_VARIANT(extern, float, HFS_VI_COS, true)
 
 // ---------------------------------------------------------------------------
 // diagnostics: norm and energy (FP64 accumulation)
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E>
+template <typename R, int N, int E, bool ALT>
 __device__ __forceinline__ void diag_item(const Diag1DArgs &a, const WorkItem &it, cpx<R> *smem)
 {
     constexpr int T = N / E;
@@ -39,7 +43,7 @@ __device__ __forceinline__ void diag_item(const Diag1DArgs &a, const WorkItem &i
         pot += (0.5 * ip.mu * w2 * x * x + ip.eps * vi_eval(ip.vi_kind, x, ip.vi_k)) * d;
         inter += 0.5 * ip.sigma * d * d;
     }
-    FftPlan<N, E>::template run<false, R>(v, sm, t, tw);
+    FftPlan<N, E, ALT>::template run<false, R>(v, sm, t, tw);
     const double kunit = 2.0 * 3.14159265358979323846 / ip.len[0];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -77,11 +81,12 @@ template <typename R> __global__ void __launch_bounds__(kCtaThreads) diag1d_kern
         if (w >= a.nwork) break;
         const WorkItem it = a.work[w];
         switch (it.plan) {
-#define HFS_CASE(NN, EE)                                                                                          \
-    case plan_id(NN, EE):                                                                                         \
-        diag_item<R, NN, EE>(a, it, smem);                                                                        \
+#define HFS_CASE(NN, EE, AA)                                                                                      \
+    case plan_id(NN, EE, AA):                                                                                     \
+        diag_item<R, NN, EE, AA>(a, it, smem);                                                                    \
         break;
             HFS_FOR_EACH_PLAN(HFS_CASE)
+            HFS_FOR_EACH_WIDE_PLAN(HFS_CASE)
 #undef HFS_CASE
         default:
             break;
@@ -149,26 +154,36 @@ static cudaError_t prepare_diag(bool fp64)
     return e;
 }
 
-int step1d_ctas_per_sm(bool fp64, int variant)
+template <bool WIDE> static int ctas_per_sm_f(int variant)
 {
-    if (fp64) return step1d_ctas_per_sm_t<double, -1>();
     switch (variant) {
-    case HFS_VI_NONE: return step1d_ctas_per_sm_t<float, HFS_VI_NONE>();
-    case HFS_VI_X4: return step1d_ctas_per_sm_t<float, HFS_VI_X4>();
-    case HFS_VI_COS: return step1d_ctas_per_sm_t<float, HFS_VI_COS>();
-    default: return step1d_ctas_per_sm_t<float, -1>();
+    case HFS_VI_NONE: return step1d_ctas_per_sm_t<float, HFS_VI_NONE, WIDE>();
+    case HFS_VI_X4: return step1d_ctas_per_sm_t<float, HFS_VI_X4, WIDE>();
+    case HFS_VI_COS: return step1d_ctas_per_sm_t<float, HFS_VI_COS, WIDE>();
+    default: return step1d_ctas_per_sm_t<float, -1, WIDE>();
     }
 }
 
-cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st)
+int step1d_ctas_per_sm(bool fp64, int variant, bool wide)
 {
-    if (fp64) return step1d_launch_t<double, -1>(a, grid, st);
+    if (fp64) return step1d_ctas_per_sm_t<double, -1, false>();
+    return wide ? ctas_per_sm_f<true>(variant) : ctas_per_sm_f<false>(variant);
+}
+
+template <bool WIDE> static cudaError_t launch_f(int variant, const Step1DArgs &a, int grid, cudaStream_t st)
+{
     switch (variant) {
-    case HFS_VI_NONE: return step1d_launch_t<float, HFS_VI_NONE>(a, grid, st);
-    case HFS_VI_X4: return step1d_launch_t<float, HFS_VI_X4>(a, grid, st);
-    case HFS_VI_COS: return step1d_launch_t<float, HFS_VI_COS>(a, grid, st);
-    default: return step1d_launch_t<float, -1>(a, grid, st);
+    case HFS_VI_NONE: return step1d_launch_t<float, HFS_VI_NONE, WIDE>(a, grid, st);
+    case HFS_VI_X4: return step1d_launch_t<float, HFS_VI_X4, WIDE>(a, grid, st);
+    case HFS_VI_COS: return step1d_launch_t<float, HFS_VI_COS, WIDE>(a, grid, st);
+    default: return step1d_launch_t<float, -1, WIDE>(a, grid, st);
     }
+}
+
+cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st, bool wide)
+{
+    if (fp64) return wide ? cudaErrorInvalidValue : step1d_launch_t<double, -1, false>(a, grid, st);
+    return wide ? launch_f<true>(variant, a, grid, st) : launch_f<false>(variant, a, grid, st);
 }
 
 int step1d_variant(const hfs_instance *inst, int64_t count)

@@ -227,18 +227,18 @@ template <int T> __device__ __forceinline__ float team_sum_end(float s, const fl
 
 // The transforms of the step: with the norm projection (FP32) the plain
 // twiddle table, otherwise the compensated one.
-template <bool INV, bool PROJ, int N, int E, typename R>
+template <bool INV, bool PROJ, int N, bool ALT, int E, typename R>
 __device__ __forceinline__ void fft(const Step1DArgs &a, cpx<R> (&v)[E], cpx<R> *sm, int t,
                                     const typename TwOf<R>::type *tw, int g)
 {
     if constexpr (PROJ && sizeof(R) == 4)
-        FftPlan<N, E>::template run<INV, R, 1, HFS_TEAM_SYNC, false>(v, sm, t, static_cast<const float2 *>(a.tw2),
-                                                                     1 + g);
-    else FftPlan<N, E>::template run<INV, R, 1, HFS_TEAM_SYNC>(v, sm, t, tw, 1 + g);
+        FftPlan<N, E, ALT>::template run<INV, R, 1, HFS_TEAM_SYNC, false>(v, sm, t,
+                                                                          static_cast<const float2 *>(a.tw2), 1 + g);
+    else FftPlan<N, E, ALT>::template run<INV, R, 1, HFS_TEAM_SYNC>(v, sm, t, tw, 1 + g);
 }
 
 // sub-stages [j0, j1): X_j, forward FFT, kinetic phase (+ projection), inverse FFT
-template <typename R, int VI, int N, int E, bool PROJ, typename Rec>
+template <typename R, int VI, int N, int E, bool ALT, bool PROJ, typename Rec>
 __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], int t, int g, bool active, int idx,
                                           const Rec *rec, const TeamParams<R> &tp, cpx<R> *sm,
                                           const typename TwOf<R>::type *tw, const float *vt, float *slots)
@@ -260,7 +260,7 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
         float dsum = 0.0f;
         xphase<N, E, VI>(v, tl, rc, tp, vt, dsum);
         if constexpr (PROJ) dsum = team_sum_begin<T>(dsum, slots);
-        fft<false, PROJ, N>(a, v, sm, tl, tw, g);
+        fft<false, PROJ, N, ALT>(a, v, sm, tl, tw, g);
         float C = 1.0f;
         if constexpr (PROJ) {
             const float s = team_sum_end<T>(dsum, slots, g);
@@ -272,11 +272,11 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
             }
         }
         kphase<N, E, PROJ>(v, tl, rc, C);
-        fft<true, PROJ, N>(a, v, sm, tl, tw, g);
+        fft<true, PROJ, N, ALT>(a, v, sm, tl, tw, g);
     }
 }
 
-template <typename R, int VI, int N, int E>
+template <typename R, int VI, int N, int E, bool ALT>
 __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
 {
     using Rec = typename RecOf<R>::type;
@@ -304,10 +304,10 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         for (int e = 0; e < E; ++e) vt[t + T * e] = eps_vi<VI>((float)(t + T * e - N / 2), tp);
     }
     if constexpr (sizeof(R) == 4) {
-        if (a.proj != PROJ_OFF) step_loop<R, VI, N, E, true>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
-        else step_loop<R, VI, N, E, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
+        if (a.proj != PROJ_OFF) step_loop<R, VI, N, E, ALT, true>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
+        else step_loop<R, VI, N, E, ALT, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
     } else {
-        step_loop<R, VI, N, E, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
+        step_loop<R, VI, N, E, ALT, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
     }
     if (a.final_x) {
         const Rec rc = rec[a.j1];
@@ -325,9 +325,14 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     }
 }
 
+// (N, E, ALT) of the plans in every step kernel, and of those only in the
+// wide kernels (alternative radix orders, four values per thread)
 #define HFS_FOR_EACH_PLAN(X)                                                                                      \
-    X(4096, 16) X(2048, 16) X(1024, 16) X(512, 16) X(256, 16) X(128, 16) X(2048, 8) X(1024, 8) X(512, 8)        \
-        X(256, 8) X(128, 8)
+    X(4096, 16, false) X(2048, 16, false) X(1024, 16, false) X(512, 16, false) X(256, 16, false)                 \
+        X(128, 16, false) X(2048, 8, false) X(1024, 8, false) X(512, 8, false) X(256, 8, false) X(128, 8, false)
+#define HFS_FOR_EACH_WIDE_PLAN(X)                                                                                 \
+    X(4096, 16, true) X(2048, 16, true) X(1024, 16, true) X(512, 16, true) X(256, 16, true) X(128, 16, true)     \
+        X(1024, 4, false) X(512, 4, false) X(256, 4, false) X(128, 4, false)
 
 // FP32: two CTAs per SM (128 registers); FP64 parity mode: one
 #ifndef HFS_STEP1D_MIN_CTAS
@@ -335,7 +340,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 #endif
 template <typename R> struct MinCtas { static constexpr int value = sizeof(R) == 4 ? HFS_STEP1D_MIN_CTAS : 1; };
 
-template <typename R, int VI>
+template <typename R, int VI, bool WIDE>
 __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(const Step1DArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -348,14 +353,29 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
         if (w >= a.nwork) break;
         const WorkItem it = a.work[w];
         switch (it.plan) {
-#define HFS_CASE(NN, EE)                                                                                          \
-    case plan_id(NN, EE):                                                                                         \
-        step_item<R, VI, NN, EE>(a, it, smem);                                                                    \
+#define HFS_CASE(NN, EE, AA)                                                                                      \
+    case plan_id(NN, EE, AA):                                                                                     \
+        step_item<R, VI, NN, EE, AA>(a, it, smem);                                                                \
         break;
             HFS_FOR_EACH_PLAN(HFS_CASE)
 #undef HFS_CASE
-        default:
-            if (threadIdx.x == 0) atomicOr(a.status, (unsigned)ST_BADPLAN);
+        default: {
+            bool handled = false;
+            if constexpr (WIDE) {
+                switch (it.plan) {
+#define HFS_CASE(NN, EE, AA)                                                                                      \
+    case plan_id(NN, EE, AA):                                                                                     \
+        step_item<R, VI, NN, EE, AA>(a, it, smem);                                                                \
+        handled = true;                                                                                           \
+        break;
+                    HFS_FOR_EACH_WIDE_PLAN(HFS_CASE)
+#undef HFS_CASE
+                default:
+                    break;
+                }
+            }
+            if (!handled && threadIdx.x == 0) atomicOr(a.status, (unsigned)ST_BADPLAN);
+        }
         }
         __syncthreads();
     }
@@ -367,37 +387,38 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
 // ---------------------------------------------------------------------------
 size_t step1d_smem_bytes(bool fp64);
 
-template <typename R, int VI> cudaError_t step1d_prepare_t()
+template <typename R, int VI, bool WIDE> cudaError_t step1d_prepare_t()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(step1d_kernel<R, VI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(step1d_kernel<R, VI, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)step1d_smem_bytes(sizeof(R) == 8));
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-template <typename R, int VI> int step1d_ctas_per_sm_t()
+template <typename R, int VI, bool WIDE> int step1d_ctas_per_sm_t()
 {
-    if (step1d_prepare_t<R, VI>() != cudaSuccess) return 1;
+    if (step1d_prepare_t<R, VI, WIDE>() != cudaSuccess) return 1;
     int n = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step1d_kernel<R, VI>, kCtaThreads,
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step1d_kernel<R, VI, WIDE>, kCtaThreads,
                                                                         step1d_smem_bytes(sizeof(R) == 8));
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
-template <typename R, int VI> cudaError_t step1d_launch_t(const Step1DArgs &a, int grid, cudaStream_t st)
+template <typename R, int VI, bool WIDE> cudaError_t step1d_launch_t(const Step1DArgs &a, int grid, cudaStream_t st)
 {
-    const cudaError_t e = step1d_prepare_t<R, VI>();
+    const cudaError_t e = step1d_prepare_t<R, VI, WIDE>();
     if (e != cudaSuccess) return e;
-    step1d_kernel<R, VI><<<grid, kCtaThreads, step1d_smem_bytes(sizeof(R) == 8), st>>>(a);
+    step1d_kernel<R, VI, WIDE><<<grid, kCtaThreads, step1d_smem_bytes(sizeof(R) == 8), st>>>(a);
     return cudaGetLastError();
 }
 
 // explicit instantiations: the generic kernels in hfs_step1d.cu, one
-// specialised FP32 kernel per perturbation kind in hfs_step1d_vi*.cu
-#define HFS_STEP1D_VARIANT(EXTERN, R, VI)                                                                         \
-    EXTERN template cudaError_t step1d_launch_t<R, VI>(const Step1DArgs &, int, cudaStream_t);                 \
-    EXTERN template int step1d_ctas_per_sm_t<R, VI>();
+// specialised FP32 kernel per perturbation kind in hfs_step1d_vi*.cu, the
+// wide FP32 kernels in hfs_step1d_wide*.cu
+#define HFS_STEP1D_VARIANT(EXTERN, R, VI, WIDE)                                                                   \
+    EXTERN template cudaError_t step1d_launch_t<R, VI, WIDE>(const Step1DArgs &, int, cudaStream_t);           \
+    EXTERN template int step1d_ctas_per_sm_t<R, VI, WIDE>();
 
 }  // namespace hfs

@@ -4,5 +4,5 @@
 #include "hfs_step1d.cuh"
 
 namespace hfs {
-HFS_STEP1D_VARIANT(, float, HFS_VI_NONE)
+HFS_STEP1D_VARIANT(, float, HFS_VI_NONE, false)
 }  // namespace hfs

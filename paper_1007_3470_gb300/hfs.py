@@ -27,16 +27,18 @@ HFS_FLOW_LEMMA2, HFS_FLOW_CF4, HFS_FLOW_M6 = 0, 1, 2
 HFS_COMP_STRANG, HFS_COMP_SRKN6_4, HFS_COMP_NI4_82, HFS_COMP_NI5_84, HFS_COMP_CUSTOM = 0, 1, 2, 3, 4
 HFS_MODE_RESIDENT, HFS_MODE_STREAMING = 0, 1
 HFS_DFT_SIMT, HFS_DFT_TENSOR_3XTF32 = 0, 1
+HFS_PLAN_ALT_ORDER = 0x100
 
 COMPOSITIONS = {"strang": HFS_COMP_STRANG, "srkn6_4": HFS_COMP_SRKN6_4, "ni4_82": HFS_COMP_NI4_82,
                 "ni5_84": HFS_COMP_NI5_84, "custom": HFS_COMP_CUSTOM}
 
 # every symbol include/hfs.h declares
 EXPORTS = ("hfs_create", "hfs_destroy", "hfs_set_stream", "hfs_state_size", "hfs_instance_offset",
-           "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_norm_projection", "hfs_set_dft_engine", "hfs_set_graphs",
-           "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi", "hfs_step", "hfs_norm",
-           "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_autotune", "hfs_set_profiling",
-           "hfs_last_step_kernel_ms", "hfs_step1d_noalloc", "hfs_error_string")
+           "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_norm_projection",
+           "hfs_set_dft_engine", "hfs_set_graphs", "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi",
+           "hfs_step", "hfs_norm", "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_set_occupancy",
+           "hfs_autotune", "hfs_autotune_cache", "hfs_set_profiling", "hfs_last_step_kernel_ms",
+           "hfs_step1d_noalloc", "hfs_error_string")
 
 
 class hfs_instance(ctypes.Structure):
@@ -96,6 +98,8 @@ def lib():
             "hfs_sync_status": [vp],
             "hfs_set_plan": [vp, i32, i32],
             "hfs_autotune": [vp, i32, ctypes.POINTER(ctypes.c_int32)],
+            "hfs_set_occupancy": [vp, i32],
+            "hfs_autotune_cache": [vp, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i32)],
             "hfs_set_profiling": [vp, i32],
             "hfs_last_step_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
             "hfs_step1d_noalloc": [vp, i32, ctypes.POINTER(hfs_instance), i64, i32, i32, i32, dbl, dbl, i64, vp, i32],
@@ -251,14 +255,29 @@ def hfs_sync_status(h) -> int:
     return lib().hfs_sync_status(h)
 
 
-def hfs_set_plan(h, n: int, elems_per_thread: int):
-    _check(lib().hfs_set_plan(h, n, elems_per_thread), "hfs_set_plan")
+def hfs_set_plan(h, n: int, plan: int):
+    """plan: elements per thread (4, 8, 16), | HFS_PLAN_ALT_ORDER for the
+    alternative radix order of 16."""
+    _check(lib().hfs_set_plan(h, n, plan), "hfs_set_plan")
+
+
+def hfs_set_occupancy(h, ctas_per_sm: int):
+    _check(lib().hfs_set_occupancy(h, ctas_per_sm), "hfs_set_occupancy")
 
 
 def hfs_autotune(h, trial_steps: int) -> list[int]:
     best = (ctypes.c_int32 * 6)()
     _check(lib().hfs_autotune(h, trial_steps, best), "hfs_autotune")
     return list(best)
+
+
+def hfs_autotune_cache(h, path: str, trial_steps: int) -> tuple[list[int], bool]:
+    """(plans per grid size 128 ... 4096, whether they came from the cache)."""
+    best = (ctypes.c_int32 * 6)()
+    hit = ctypes.c_int()
+    _check(lib().hfs_autotune_cache(h, os.fsencode(path), trial_steps, best, ctypes.byref(hit)),
+           "hfs_autotune_cache")
+    return list(best), bool(hit.value)
 
 
 def hfs_set_profiling(h, enable: bool):
@@ -392,8 +411,12 @@ class Solver:
     def status(self) -> int:
         return hfs_sync_status(self.h)
 
-    def autotune(self, trial_steps: int = 20) -> list[int]:
-        return hfs_autotune(self.h, trial_steps)
+    def autotune(self, trial_steps: int = 20, cache: Optional[str] = None) -> list[int]:
+        """Tune the 1D plans; with `cache`, reuse (or record) them in that JSON file."""
+        if cache is None:
+            return hfs_autotune(self.h, trial_steps)
+        plans, self.tune_cache_hit = hfs_autotune_cache(self.h, cache, trial_steps)
+        return plans
 
     def set_plan(self, n: int, ept: int):
         hfs_set_plan(self.h, n, ept)
