@@ -228,14 +228,17 @@ __device__ __forceinline__ cpx<double> apply_turns(cpx<double> u, double turns, 
     return {u.x * c + u.y * s, u.y * c - u.x * s};
 }
 
-// the perturbation V_I(x) of one axis
+// the perturbation V_I(x) of one axis; the accurate cosf (the fast intrinsic's
+// error grows with the argument, and |k x| reaches a few hundred radians on
+// the wide batched boxes).  Kernels evaluate it once per grid point and keep
+// it in shared memory, not per step.
 __device__ __forceinline__ float vi_eval(int kind, float x, float k)
 {
     if (kind == HFS_VI_X4) {
         const float x2 = x * x;
         return x2 * x2;
     }
-    if (kind == HFS_VI_COS) return __cosf(k * x);
+    if (kind == HFS_VI_COS) return cosf(k * x);
     return 0.0f;
 }
 

@@ -264,6 +264,13 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
     constexpr int N = kPlaneN, E = 16, T = N / E, LINES = kPlaneThreads / T;  // 64 lines per round
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<float> *pl = reinterpret_cast<cpx<float> *>(smem_raw);
+    // eps V_I(x_j) of the plane's x-columns, evaluated once per launch
+    __shared__ float s_vx[N];
+    if constexpr (MODE & P_PHASE) {
+        const DevInst &ip = *a.inst;
+        for (int i = threadIdx.x; i < N; i += kPlaneThreads)
+            s_vx[i] = (float)ip.eps * vi_eval(VI, (float)(i - N / 2) * (float)ip.dx[0], (float)ip.vi_k);
+    }
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
     const auto *tw = reinterpret_cast<const float4 *>(a.tw);
@@ -315,9 +322,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
                 const float tyz = turns_q(my, rc.k2[1], rc.k2lo[1]) + tz;
                 const float vyz = vi_eval(vkind, (float)my * (float)ip.dx[1], vk) + vz;
                 // points in pairs, the phase arithmetic in packed FP32 (bit-identical)
+                const float evyz = eps * vyz;
                 auto Fof = [&](const cpx<float> &u, int mx) {
                     const float dens = u.x * u.x + u.y * u.y;
-                    return sig * dens + eps * (vi_eval(vkind, (float)mx * dx, vk) + vyz);
+                    return sig * dens + (s_vx[mx + N / 2] + evyz);
                 };
 #pragma unroll
                 for (int e = 0; e < E; e += 2) {
