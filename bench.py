@@ -432,7 +432,7 @@ def run_native(args):
     solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS_)
     solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     solver.set_norm_projection(not args.no_projection)
-    tuned, tuned_from = tune(solver, 20) if args.autotune else (None, None)
+    tuned, tuned_from = tune(solver, 100) if args.autotune else (None, None)
     hfs.hfs_set_profiling(solver.h, True)
     solver.set_graphs(True)
     host0 = np.concatenate([p.astype(np.complex64) for p in psis])

@@ -235,15 +235,14 @@ int hfs_set_plan(hfs_ctx_t ctx, int n, int plan);
  * default; values above that are clamped). */
 int hfs_set_occupancy(hfs_ctx_t ctx, int ctas_per_sm);
 
-/* Search the 1D plans with CUDA-event timings of trial_steps steps each in
- * the current mode (resident or streaming) and keep the fastest: per grid
- * size present, every admissible plan (16, 8, 4 values per thread, the
- * alternative radix order) on that size's work items alone; then the whole
- * batch with the chosen plans against the default kernel's plans (a wide
- * plan moves the launch to the larger wide kernel) and one CTA per SM
- * against as many as fit.  Overwrites the state: call before hfs_set_psi.
- * best_plans[6] (host, may be NULL) receives the chosen plan (as for
- * hfs_set_plan) for n = 128 ... 4096, 0 where the size is absent. */
+/* Search the 1D plans with CUDA-event timings of trial_steps steps of the
+ * whole batch in the current mode (resident or streaming): coordinate
+ * descent, two rounds over the grid sizes present, each trying every
+ * admissible plan of that size (16, 8, 4 values per thread, the alternative
+ * radix order) with the others fixed, keeping the fastest batch time; then
+ * one CTA per SM against as many as fit.  Overwrites the state: call before
+ * hfs_set_psi.  best_plans[6] (host, may be NULL) receives the chosen plan
+ * (as for hfs_set_plan) for n = 128 ... 4096, 0 where the size is absent. */
 int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_plans);
 
 /* hfs_autotune with a persistent cache: the JSON file at `path` holds tuned

@@ -834,23 +834,30 @@ namespace {
 int encode_plan(const hfs_ctx_s *c, int k) { return c->ept[k] | (c->alt[k] ? HFS_PLAN_ALT_ORDER : 0); }
 
 // time `steps` steps of the current work list (resident or streaming as
-// set); the first of two runs warms up
+// set): one warm-up run, then the best of two
 int time_worklist(hfs_ctx_s *c, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, float *ms)
 {
     int s = upload_tables(c);
     if (s) return s;
-    for (int rep = 0; rep < 2; ++rep) {
+    *ms = INFINITY;
+    for (int rep = 0; rep < 3; ++rep) {
         CK(cudaEventRecord(e0, c->stream));
         s = enqueue_steps(c, steps);
         if (s) return s;
         CK(cudaEventRecord(e1, c->stream));
         CK(cudaEventSynchronize(e1));
-        CK(cudaEventElapsedTime(ms, e0, e1));
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) *ms = std::min(*ms, t);
     }
     return HFS_OK;
 }
 
-// The search of hfs_autotune (see include/hfs.h).
+// The search of hfs_autotune (see include/hfs.h): coordinate descent over
+// the grid sizes present, every candidate timed on the WHOLE batch (a size
+// class alone under-fills the GPU and favours plans with more, smaller
+// teams; a wide plan anywhere also moves the launch to the wide kernel),
+// two rounds; then one CTA per SM against as many as fit.
 int autotune(hfs_ctx_s *c, int trial_steps, float *best_total)
 {
     const int64_t steps = std::min<int64_t>(trial_steps, c->chunk);
@@ -865,70 +872,40 @@ int autotune(hfs_ctx_s *c, int trial_steps, float *best_total)
     CK(cudaEventCreate(&e1));
     const bool fp32 = c->precision == HFS_C64;
     int s = HFS_OK;
-    // 1. per size class, each plan timed on that class's work items alone
-    const int cand[4] = {16, 8, 16 | HFS_PLAN_ALT_ORDER, 4};
-    for (int k = 0; k < kNumSizes && !s; ++k) {
-        if (!present[k]) continue;
-        const int n = 128 << k;
-        float best = INFINITY;
-        int best_plan = encode_plan(c, k);
-        for (int ci = 0; ci < 4 && !s; ++ci) {
-            const int plan = cand[ci], ept = plan & 0xff;
-            const bool alt = (plan & HFS_PLAN_ALT_ORDER) != 0;
-            if ((ept == 8 && n > 2048) || (ept == 4 && n > 1024)) continue;
-            if ((ept == 4 || alt) && !fp32) continue;
-            c->ept[k] = ept;
-            c->alt[k] = alt;
-            build_worklist(c);
-            std::vector<WorkItem> keep;
-            for (auto &w : c->work)
-                if (w.plan == plan_id(n, ept, alt)) keep.push_back(w);
-            c->work.swap(keep);
-            float ms = 0.0f;
-            s = time_worklist(c, steps, e0, e1, &ms);
-            if (!s && ms < best) {
-                best = ms;
-                best_plan = plan;
-            }
-        }
-        c->ept[k] = best_plan & 0xff;
-        c->alt[k] = (best_plan & HFS_PLAN_ALT_ORDER) != 0;
-    }
-    // 2. the whole batch: the chosen plans against the best of the default
-    //    kernel's plans alone (a wide plan anywhere moves the whole launch to
-    //    the wide kernel), then 1 CTA per SM against as many as fit
     float total = INFINITY;
-    if (!s) {
-        build_worklist(c);
-        s = time_worklist(c, steps, e0, e1, &total);
-    }
-    if (!s && worklist_wide(c)) {
-        int save_e[kNumSizes];
-        bool save_a[kNumSizes];
-        std::copy(c->ept, c->ept + kNumSizes, save_e);
-        std::copy(c->alt, c->alt + kNumSizes, save_a);
-        // best default-kernel plan per class: the chosen one if it is not
-        // wide, else 16 values per thread
-        for (int k = 0; k < kNumSizes; ++k)
-            if (c->alt[k] || c->ept[k] == 4) {
-                c->ept[k] = 16;
-                c->alt[k] = false;
+    build_worklist(c);
+    s = time_worklist(c, steps, e0, e1, &total);
+    const int cand[4] = {16, 8, 16 | HFS_PLAN_ALT_ORDER, 4};
+    for (int round = 0; round < 2 && !s; ++round) {
+        for (int k = 0; k < kNumSizes && !s; ++k) {
+            if (!present[k]) continue;
+            const int n = 128 << k;
+            const int keep = encode_plan(c, k);
+            int best_plan = keep;
+            for (int ci = 0; ci < 4 && !s; ++ci) {
+                const int plan = cand[ci], ept = plan & 0xff;
+                const bool alt = (plan & HFS_PLAN_ALT_ORDER) != 0;
+                if (plan == keep || (ept == 8 && n > 2048) || (ept == 4 && n > 1024)) continue;
+                if ((ept == 4 || alt) && !fp32) continue;
+                c->ept[k] = ept;
+                c->alt[k] = alt;
+                build_worklist(c);
+                float ms = 0.0f;
+                s = time_worklist(c, steps, e0, e1, &ms);
+                if (!s && ms < total) {
+                    total = ms;
+                    best_plan = plan;
+                }
             }
-        build_worklist(c);
-        float ms = 0.0f;
-        s = time_worklist(c, steps, e0, e1, &ms);
-        if (!s && ms < total) {
-            total = ms;
-        } else {
-            std::copy(save_e, save_e + kNumSizes, c->ept);
-            std::copy(save_a, save_a + kNumSizes, c->alt);
+            c->ept[k] = best_plan & 0xff;
+            c->alt[k] = (best_plan & HFS_PLAN_ALT_ORDER) != 0;
         }
     }
     if (!s) {
         // one CTA per SM against the current setting (as many as fit)
         build_worklist(c);
         const int keep = c->ctas_per_sm;
-        c->ctas_per_sm = 1;
+        c->ctas_per_sm = keep == 1 ? 0 : 1;
         float ms = 0.0f;
         s = time_worklist(c, steps, e0, e1, &ms);
         if (!s && ms < total) total = ms;
