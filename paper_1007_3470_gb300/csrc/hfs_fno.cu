@@ -159,6 +159,13 @@ GemmArgs gemm(int M, int N, int K, const bf16 *A, int64_t lda, const bf16 *B, in
 cudaError_t run(const GemmArgs &g, bool ta, bool tb, cudaStream_t st)
 {
     const dim3 grid((g.N + GT_N - 1) / GT_N, (g.M + GT_M - 1) / GT_M, g.batch * g.splitk);
+    if (gemm_pipe_ok(g, ta, tb)) {
+        if (!ta && !tb) gemm_bf16_pipe_kernel<false, false><<<grid, 128, 0, st>>>(g);
+        else if (ta && !tb) gemm_bf16_pipe_kernel<true, false><<<grid, 128, 0, st>>>(g);
+        else if (!ta && tb) gemm_bf16_pipe_kernel<false, true><<<grid, 128, 0, st>>>(g);
+        else gemm_bf16_pipe_kernel<true, true><<<grid, 128, 0, st>>>(g);
+        return cudaGetLastError();
+    }
     if (!ta && !tb) gemm_bf16_kernel<false, false><<<grid, 128, 0, st>>>(g);
     else if (ta && !tb) gemm_bf16_kernel<true, false><<<grid, 128, 0, st>>>(g);
     else if (!ta && tb) gemm_bf16_kernel<false, true><<<grid, 128, 0, st>>>(g);

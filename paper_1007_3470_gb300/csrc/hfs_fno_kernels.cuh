@@ -167,6 +167,198 @@ template <bool TA, bool TB> __global__ void __launch_bounds__(128) gemm_bf16_ker
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined form of the same GEMM (same arguments, tiles and epilogue): the
+// tiles of op(A) and op(B) stream into a three-stage shared-memory ring by
+// 16-byte asynchronous copies (cp.async, zero-filled outside the matrix), so
+// the loads of tile k + 2 overlap the MMAs of tile k; an operand stored with
+// its contiguous dimension along m or n stays in that layout in shared
+// memory and is read with ldmatrix.trans (no element-wise transposition).
+// Eligible when every 16-byte chunk is all in or all out of range: leading
+// dimensions, batch strides and base addresses in whole 8-element chunks,
+// and the chunked extents (K; M for a transposed A; N for a row-major B)
+// multiples of 8 (gemm_pipe_ok).
+// ---------------------------------------------------------------------------
+constexpr int GP_STAGES = 3, GP_LDT = 72;  // transposed tiles: [32 k][64 + 8]
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const bf16 *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned (&r)[2], const bf16 *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+// 16-byte asynchronous copy; an invalid chunk is zero-filled (source size 0)
+__device__ __forceinline__ void cp16(bf16 *dst, const bf16 *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+inline bool gemm_pipe_ok(const GemmArgs &g, bool ta, bool tb)
+{
+    auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al(g.A) || !al(g.B) || g.lda % 8 || g.ldb % 8 || g.sA % 8 || g.sB % 8) return false;
+    if (g.K % 8) return false;
+    if (ta && g.M % 8) return false;
+    if (!tb && g.N % 8) return false;
+    return true;
+}
+
+template <bool TA, bool TB> __global__ void __launch_bounds__(128) gemm_bf16_pipe_kernel(const GemmArgs g)
+{
+    constexpr int A_EL = TA ? GT_K * GP_LDT : GT_M * GT_LD;
+    constexpr int B_EL = TB ? GT_N * GT_LD : GT_K * GP_LDT;
+    __shared__ __align__(128) bf16 sA[GP_STAGES][A_EL];
+    __shared__ __align__(128) bf16 sB[GP_STAGES][B_EL];
+    const int n0 = blockIdx.x * GT_N, m0 = blockIdx.y * GT_M;
+    const int b = blockIdx.z / g.splitk, kz = blockIdx.z % g.splitk;
+    const int kper = ((g.K + g.splitk - 1) / g.splitk + GT_K - 1) / GT_K * GT_K;
+    const int kbeg = kz * kper, kend = min(g.K, kbeg + kper);
+    const int nk = kend > kbeg ? (kend - kbeg + GT_K - 1) / GT_K : 0;
+    const bf16 *A = g.A + (int64_t)b * g.sA;
+    const bf16 *B = g.B + (int64_t)b * g.sB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+
+    auto load_stage = [&](int st, int k0) {
+        // 256 chunks of 8 elements per operand tile, two per thread
+#pragma unroll
+        for (int c = threadIdx.x; c < 256; c += 128) {
+            if constexpr (!TA) {
+                const int r = c >> 2, kc = (c & 3) * 8, row = m0 + r, k = k0 + kc;
+                const bool ok = row < g.M && k + 8 <= kend;
+                cp16(&sA[st][r * GT_LD + kc], ok ? A + (int64_t)row * g.lda + k : A, ok);
+            } else {
+                const int kk = c >> 3, mc = (c & 7) * 8, k = k0 + kk, m = m0 + mc;
+                const bool ok = k < kend && m < g.M;
+                cp16(&sA[st][kk * GP_LDT + mc], ok ? A + (int64_t)k * g.lda + m : A, ok);
+            }
+            if constexpr (TB) {
+                const int r = c >> 2, kc = (c & 3) * 8, row = n0 + r, k = k0 + kc;
+                const bool ok = row < g.N && k + 8 <= kend;
+                cp16(&sB[st][r * GT_LD + kc], ok ? B + (int64_t)row * g.ldb + k : B, ok);
+            } else {
+                const int kk = c >> 3, nc = (c & 7) * 8, k = k0 + kk, n = n0 + nc;
+                const bool ok = k < kend && n < g.N;
+                cp16(&sB[st][kk * GP_LDT + nc], ok ? B + (int64_t)k * g.ldb + n : B, ok);
+            }
+        }
+    };
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < GP_STAGES - 1; ++s) {
+        if (s < nk) load_stage(s, kbeg + s * GT_K);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(GP_STAGES - 2) : "memory");
+        __syncthreads();  // tile kt visible to all; stage (kt - 1) % S no longer read
+        if (kt + GP_STAGES - 1 < nk) load_stage((kt + GP_STAGES - 1) % GP_STAGES, kbeg + (kt + GP_STAGES - 1) * GT_K);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const bf16 *a_s = sA[kt % GP_STAGES];
+        const bf16 *b_s = sB[kt % GP_STAGES];
+#pragma unroll
+        for (int kk = 0; kk < GT_K; kk += 16) {
+            unsigned af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                if constexpr (!TA)
+                    ldsm_x4(af[mi], a_s + (wm + mi * 16 + (lane & 15)) * GT_LD + kk + (lane >> 4) * 8);
+                else
+                    ldsm_x4_t(af[mi], a_s + (kk + (lane & 7) + ((lane >> 4) & 1) * 8) * GP_LDT + wm + mi * 16 +
+                                          ((lane >> 3) & 1) * 8);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                if constexpr (TB)
+                    ldsm_x2(bfr[ni], b_s + (wn + ni * 8 + (lane & 7)) * GT_LD + kk + ((lane >> 3) & 1) * 8);
+                else
+                    ldsm_x2_t(bfr[ni], b_s + (kk + (lane & 7) + ((lane >> 3) & 1) * 8) * GP_LDT + wn + ni * 8);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // epilogue (as gemm_bf16_kernel), the two adjacent columns (n, n + 1) of
+    // an accumulator pair stored together when every output allows it
+    auto even = [](int64_t v) { return (v & 1) == 0; };
+    auto al8 = [](const void *p) { return ((uintptr_t)p & 7) == 0; };
+    const bool vec = g.splitk == 1 && even(g.N) && (!g.C || (al8(g.C) && even(g.ldc) && even(g.sC))) &&
+                     (!g.Cb || ((((uintptr_t)g.Cb & 3) == 0) && even(g.ldcb) && even(g.sCb))) &&
+                     (!g.pre || (al8(g.pre) && even(g.ldp) && even(g.sP))) &&
+                     (!g.add || (al8(g.add) && even(g.ldadd) && even(g.sAdd))) && (!g.bias || al8(g.bias));
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm + mi * 16 + (lane >> 2) + h * 8;
+                const int n = n0 + wn + ni * 8 + (lane & 3) * 2;
+                if (m >= g.M || n >= g.N) continue;
+                float2 v = make_float2(g.alpha * acc[mi][ni][2 * h], g.alpha * acc[mi][ni][2 * h + 1]);
+                if (vec) {
+                    const int64_t oc = (int64_t)b * g.sC + (int64_t)m * g.ldc + n;
+                    if (g.beta) {
+                        const float2 c0 = *reinterpret_cast<const float2 *>(g.C + oc);
+                        v.x += c0.x;
+                        v.y += c0.y;
+                    }
+                    if (g.bias) {
+                        const float2 bb = *reinterpret_cast<const float2 *>(g.bias + n);
+                        v.x += bb.x;
+                        v.y += bb.y;
+                    }
+                    if (g.add) {
+                        const float2 ad =
+                            *reinterpret_cast<const float2 *>(g.add + (int64_t)b * g.sAdd + (int64_t)m * g.ldadd + n);
+                        v.x += ad.x;
+                        v.y += ad.y;
+                    }
+                    if (g.pre) *reinterpret_cast<float2 *>(g.pre + (int64_t)b * g.sP + (int64_t)m * g.ldp + n) = v;
+                    if (g.gelu) v = make_float2(gelu_f(v.x), gelu_f(v.y));
+                    if (g.C) *reinterpret_cast<float2 *>(g.C + oc) = v;
+                    if (g.Cb)
+                        *reinterpret_cast<__nv_bfloat162 *>(g.Cb + (int64_t)b * g.sCb + (int64_t)m * g.ldcb + n) =
+                            __floats2bfloat162_rn(v.x, v.y);
+                    continue;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int nq = n + q;
+                    if (nq >= g.N) continue;
+                    float w = q ? v.y : v.x;
+                    if (g.splitk > 1) {
+                        atomicAdd(g.C + (int64_t)b * g.sC + (int64_t)m * g.ldc + nq, w);
+                        continue;
+                    }
+                    if (g.beta) w += g.C[(int64_t)b * g.sC + (int64_t)m * g.ldc + nq];
+                    if (g.bias) w += g.bias[nq];
+                    if (g.add) w += g.add[(int64_t)b * g.sAdd + (int64_t)m * g.ldadd + nq];
+                    if (g.pre) g.pre[(int64_t)b * g.sP + (int64_t)m * g.ldp + nq] = w;
+                    if (g.gelu) w = gelu_f(w);
+                    if (g.C) g.C[(int64_t)b * g.sC + (int64_t)m * g.ldc + nq] = w;
+                    if (g.Cb) g.Cb[(int64_t)b * g.sCb + (int64_t)m * g.ldcb + nq] = __float2bfloat16(w);
+                }
+            }
+}
+
+// ---------------------------------------------------------------------------
 // elementwise and reductions
 // ---------------------------------------------------------------------------
 
