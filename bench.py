@@ -239,7 +239,7 @@ def extra_measurements(hfs, W, torch):
     ss.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     ss.set_norm_projection(True)
     ss.set_mode(hfs.HFS_MODE_STREAMING, 1)
-    tune(ss, 2)
+    tune(ss, 8)
     ss.set_graphs(True)
     ss.set_psi(psis)
     ms = kernel_ms(ss, STEPS)
@@ -344,8 +344,8 @@ def hbm_streaming_measurement(hfs, W, count: int = 65536, steps: int = 20):
     s.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     s.set_norm_projection(True)
     s.set_mode(hfs.HFS_MODE_STREAMING, 1)
-    # plans per grid size measured in this mode (2 trial steps per candidate)
-    tuned, _ = tune(s, 2)
+    # plans per grid size measured in this mode (8 trial steps per candidate)
+    tuned, _ = tune(s, 8)
     s.set_graphs(True)
     hfs.hfs_set_profiling(s.h, True)
     s.set_psi(psis)

@@ -281,8 +281,9 @@ int hfs_last_step_kernel_ms(hfs_ctx_t ctx, float *ms);
  * complex128 for HFS_C128, 8/16-byte aligned; read and overwritten in place)
  * by nsteps steps of size dt from time t0, with the given split, harmonic
  * flow and built-in composition (HFS_COMP_CUSTOM is not accepted), on the
- * given stream (NULL: legacy default stream).  Results equal those of
- * hfs_step() with a 16-step schedule chunk.
+ * given stream (NULL: legacy default stream).  Results equal, bit for bit,
+ * those of hfs_step() with a 16-step schedule chunk and the context's
+ * defaults (16 values per thread, norm projection off).
  *
  * No device memory is allocated or freed: all scratch lives in one
  * file-scope __device__ array of HFS_NOALLOC_SCRATCH_BYTES that every GPU
