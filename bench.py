@@ -64,7 +64,8 @@ STEP1D_TRAFFIC = {"src": "f412f2c592439c6c",
                   "batch_1d_4096x500_c64": 110522368 + 47401472,
                   "batch_1d_65536x1_streaming": (733481472 + 796048896 + 733453568 + 792685824) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cuh", "hfs_step1d.cu", "hfs_step1d_vicos.cu", "hfs_step1d_vix4.cu", "hfs_step1d_vinone.cu",
-                  "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_sched.h")
+                  "hfs_step1d_wide.cu", "hfs_step1d_wide_vicos.cu", "hfs_step1d_wide_vix4.cu",
+                  "hfs_step1d_wide_vinone.cu", "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_sched.h")
 
 
 def step1d_traffic(workload: str):
@@ -432,7 +433,9 @@ def run_native(args):
     solver = hfs.Solver(insts, precision="c64", chunk_steps=STEPS_)
     solver.set_schedule(DT, "strang", hfs.HFS_FLOW_CF4)
     solver.set_norm_projection(not args.no_projection)
-    tuned, tuned_from = tune(solver, 100) if args.autotune else (None, None)
+    # candidates timed on full-length solves (shorter trials keep the phase
+    # records in L2 and misjudge the plans)
+    tuned, tuned_from = tune(solver, STEPS_) if args.autotune else (None, None)
     hfs.hfs_set_profiling(solver.h, True)
     solver.set_graphs(True)
     host0 = np.concatenate([p.astype(np.complex64) for p in psis])

@@ -276,7 +276,7 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
     }
 }
 
-template <typename R, int VI, int N, int E, bool ALT>
+template <typename R, int VI, int N, int E, bool ALT, bool PROJ>
 __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
 {
     using Rec = typename RecOf<R>::type;
@@ -303,12 +303,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 #pragma unroll
         for (int e = 0; e < E; ++e) vt[t + T * e] = eps_vi<VI>((float)(t + T * e - N / 2), tp);
     }
-    if constexpr (sizeof(R) == 4) {
-        if (a.proj != PROJ_OFF) step_loop<R, VI, N, E, ALT, true>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
-        else step_loop<R, VI, N, E, ALT, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
-    } else {
-        step_loop<R, VI, N, E, ALT, false>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
-    }
+    step_loop<R, VI, N, E, ALT, PROJ && sizeof(R) == 4>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
     if (a.final_x) {
         const Rec rc = rec[a.j1];
         float dsum = 0.0f;
@@ -340,7 +335,10 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 #endif
 template <typename R> struct MinCtas { static constexpr int value = sizeof(R) == 4 ? HFS_STEP1D_MIN_CTAS : 1; };
 
-template <typename R, int VI, bool WIDE>
+// PROJ: the norm projection (its loop and the plain twiddle table); a kernel
+// holds one of the two loops per plan, not both, to keep its instruction
+// footprint down
+template <typename R, int VI, bool WIDE, bool PROJ>
 __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(const Step1DArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -355,7 +353,7 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
         switch (it.plan) {
 #define HFS_CASE(NN, EE, AA)                                                                                      \
     case plan_id(NN, EE, AA):                                                                                     \
-        step_item<R, VI, NN, EE, AA>(a, it, smem);                                                                \
+        step_item<R, VI, NN, EE, AA, PROJ>(a, it, smem);                                                          \
         break;
             HFS_FOR_EACH_PLAN(HFS_CASE)
 #undef HFS_CASE
@@ -365,7 +363,7 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
                 switch (it.plan) {
 #define HFS_CASE(NN, EE, AA)                                                                                      \
     case plan_id(NN, EE, AA):                                                                                     \
-        step_item<R, VI, NN, EE, AA>(a, it, smem);                                                                \
+        step_item<R, VI, NN, EE, AA, PROJ>(a, it, smem);                                                          \
         handled = true;                                                                                           \
         break;
                     HFS_FOR_EACH_WIDE_PLAN(HFS_CASE)
@@ -391,8 +389,11 @@ template <typename R, int VI, bool WIDE> cudaError_t step1d_prepare_t()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(step1d_kernel<R, VI, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)step1d_smem_bytes(sizeof(R) == 8));
+    const int bytes = (int)step1d_smem_bytes(sizeof(R) == 8);
+    cudaError_t e = cudaFuncSetAttribute(step1d_kernel<R, VI, WIDE, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && sizeof(R) == 4)
+        e = cudaFuncSetAttribute(step1d_kernel<R, VI, WIDE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -401,8 +402,8 @@ template <typename R, int VI, bool WIDE> int step1d_ctas_per_sm_t()
 {
     if (step1d_prepare_t<R, VI, WIDE>() != cudaSuccess) return 1;
     int n = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step1d_kernel<R, VI, WIDE>, kCtaThreads,
-                                                                        step1d_smem_bytes(sizeof(R) == 8));
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, step1d_kernel<R, VI, WIDE, false>, kCtaThreads, step1d_smem_bytes(sizeof(R) == 8));
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
@@ -410,7 +411,9 @@ template <typename R, int VI, bool WIDE> cudaError_t step1d_launch_t(const Step1
 {
     const cudaError_t e = step1d_prepare_t<R, VI, WIDE>();
     if (e != cudaSuccess) return e;
-    step1d_kernel<R, VI, WIDE><<<grid, kCtaThreads, step1d_smem_bytes(sizeof(R) == 8), st>>>(a);
+    const size_t bytes = step1d_smem_bytes(sizeof(R) == 8);
+    if (sizeof(R) == 4 && a.proj != PROJ_OFF) step1d_kernel<R, VI, WIDE, true><<<grid, kCtaThreads, bytes, st>>>(a);
+    else step1d_kernel<R, VI, WIDE, false><<<grid, kCtaThreads, bytes, st>>>(a);
     return cudaGetLastError();
 }
 
