@@ -237,7 +237,8 @@ int hfs_set_occupancy(hfs_ctx_t ctx, int ctas_per_sm);
 
 /* Search the 1D plans with CUDA-event timings of trial_steps steps of the
  * whole batch in the current mode (resident or streaming): coordinate
- * descent, two rounds over the grid sizes present, each trying every
+ * descent from 8 values per thread for n <= 1024 and 16 above, two rounds
+ * over the grid sizes present, each trying every
  * admissible plan of that size (16, 8, 4 values per thread, the alternative
  * radix order) with the others fixed, keeping the fastest batch time; then
  * one CTA per SM against as many as fit.  Overwrites the state: call before

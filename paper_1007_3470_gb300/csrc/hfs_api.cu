@@ -834,13 +834,13 @@ namespace {
 int encode_plan(const hfs_ctx_s *c, int k) { return c->ept[k] | (c->alt[k] ? HFS_PLAN_ALT_ORDER : 0); }
 
 // time `steps` steps of the current work list (resident or streaming as
-// set): one warm-up run, then the best of two
+// set): one warm-up run, then the best of three
 int time_worklist(hfs_ctx_s *c, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, float *ms)
 {
     int s = upload_tables(c);
     if (s) return s;
     *ms = INFINITY;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = 0; rep < 4; ++rep) {
         CK(cudaEventRecord(e0, c->stream));
         s = enqueue_steps(c, steps);
         if (s) return s;
@@ -873,6 +873,13 @@ int autotune(hfs_ctx_s *c, int trial_steps, float *best_total)
     const bool fp32 = c->precision == HFS_C64;
     int s = HFS_OK;
     float total = INFINITY;
+    // start point: 8 values per thread up to n = 1024 (several instances per
+    // CTA), 16 above; each size's plan moves the batch time by about 1 %,
+    // so the descent is sensitive to where it starts
+    for (int k = 0; k < kNumSizes; ++k) {
+        c->ept[k] = (128 << k) <= 1024 ? 8 : 16;
+        c->alt[k] = false;
+    }
     build_worklist(c);
     s = time_worklist(c, steps, e0, e1, &total);
     const int cand[4] = {16, 8, 16 | HFS_PLAN_ALT_ORDER, 4};
