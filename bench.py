@@ -224,6 +224,16 @@ def extra_measurements(hfs, W, torch):
                                          "hbm_equivalent_GBps_32B": hbm3,
                                          "hbm_equivalent_frac_of_measured": hbm3 / float(peaks.get("hbm_gbs", 6800.0)),
                                          "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
+    # the same with the norm projection (plain twiddles)
+    s3.set_norm_projection(True)
+    s3.set_time(0.0)
+    s3.set_psi(psi0.ravel())
+    ms_p = kernel_ms(s3, steps)
+    out["gpe3d_128cube_200steps_c64_projected"] = {
+        "kernel_ms": ms_p, "grid_point_steps_per_s": gps / (ms_p * 1e-3),
+        "hbm_equivalent_frac_of_measured": gps * 32 / (ms_p * 1e-3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+        "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
+    s3.set_norm_projection(False)
     # the same with the z-transforms' radix-16 stages on the tensor cores
     s3.set_dft_engine(hfs.HFS_DFT_TENSOR_3XTF32)
     s3.set_time(0.0)

@@ -165,9 +165,14 @@ int hfs_set_mode(hfs_ctx_t ctx, int mode, int steps_per_launch);
  * sqrt(N0 / N_j), N_0 the sum of |psi|^2 at the start of the hfs_step() call
  * and N_j the current one (both measured in FP32 inside the fused kernel),
  * which removes the radial component of the rounding error instead of
- * letting it accumulate; the paper's method itself has no such step.
- * Errors: HFS_ERR_UNSUPPORTED for 3D or complex128 contexts (their drift is
- * ~1e-8 and ~1e-14). */
+ * letting it accumulate; the paper's method itself has no such step.  With
+ * the projection the step kernels read plain FP32 twiddles (the compensated
+ * table only stops a systematic norm bias, which the projection removes).
+ * 3D (complex64, 128 points per axis): each plane pass sums |psi|^2 in its
+ * x-phase and the z-pass that follows applies the factor, the target being
+ * the sum at the start of the hfs_step() call.
+ * Errors: HFS_ERR_UNSUPPORTED for complex128 contexts (drift ~1e-14) and 3D
+ * grids other than 128^3. */
 int hfs_set_norm_projection(hfs_ctx_t ctx, int enable);
 
 /* Engine of the radix-16 DFT stages of the 3D z-transform (the first pass of

@@ -95,7 +95,7 @@ double omega_bound(const hfs_instance &p, double t0, double t1)
 namespace {
 
 struct Layout {
-    size_t status, ticket, tdev, inst, order, work, twf, twd, twp, fge, nodes, rec, diag, norm, total;
+    size_t status, ticket, tdev, inst, order, work, twf, twd, twp, fge, nodes, rec, diag, norm, nsum3, total;
 };
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -197,6 +197,7 @@ Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
     L.rec = take(recsz * c->count * (nstage + 1));
     L.diag = take(sizeof(double) * 2 * std::max<int64_t>(c->count, 1));
     L.norm = take(sizeof(float) * std::max<int64_t>(c->count, 1));
+    L.nsum3 = take(4 * sizeof(double));  // 3D projection: three sum slots and the target
     L.total = o;
     return L;
 }
@@ -358,6 +359,11 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
             a.n = c->inst[0].n[0];
             a.vi = c->inst[0].eps != 0.0 ? c->inst[0].vi_kind : HFS_VI_NONE;
             a.dft_tc = c->dft_engine == HFS_DFT_TENSOR_3XTF32 ? 1 : 0;
+            a.tw2 = wptr<void>(c, c->lay.twp);
+            a.nsum = wptr<double>(c, c->lay.nsum3);
+            a.ntarget = a.nsum + 3;
+            a.proj = !c->norm_projection ? PROJ_OFF : (done == 0 ? PROJ_SET : PROJ_USE);
+            if (a.proj != PROJ_OFF) CK(cudaMemsetAsync(a.nsum, 0, 3 * sizeof(double), c->stream));
             if (c->profiling && done == 0) CK(record_prof(c, 0));
             CK(launch_step3d(fp64, a, c->stream));
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
@@ -624,7 +630,9 @@ int hfs_set_mode(hfs_ctx_t c, int mode, int spl)
 int hfs_set_norm_projection(hfs_ctx_t c, int enable)
 {
     if (!c) return HFS_ERR_INVALID_ARG;
-    if (c->dim != 1 || c->precision != HFS_C64) return HFS_ERR_UNSUPPORTED;
+    if (c->precision != HFS_C64) return HFS_ERR_UNSUPPORTED;
+    // 3D: the plane-pass path (n = 128 per axis)
+    if (c->dim == 3 && c->inst[0].n[0] != 128) return HFS_ERR_UNSUPPORTED;
     c->norm_projection = enable != 0;
     drop_graphs(c);
     return HFS_OK;

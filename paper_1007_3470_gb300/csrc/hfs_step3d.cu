@@ -119,7 +119,43 @@ __global__ void __launch_bounds__(kCtaThreads) ypass3d(const Step3DArgs a)
 // FP32: two CTAs per SM (128 registers; at 143 registers one CTA of 8 warps
 // per SM left the column loads' latency exposed); FP64: one
 template <typename R> struct ZpassMinCtas { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
-template <typename R, int N>
+// Norm projection in 3D: the plane pass of sub-stage j adds its plane's sum
+// of |u|^2 (taken in the x-phase) to slot j mod 3; the z-pass j that follows
+// reads the complete sum, scales its k-phase by C = sqrt(target / sum), and
+// clears slot j + 1 for the next plane pass.  The first z-pass of a call
+// records the target (PROJ_SET) and applies C = 1.
+// Every thread loads the two sums at the kernel's start (the loads complete
+// behind the forward transform) and forms the factor in FP32 where the
+// k-phase needs it; no thread waits on another for it.
+struct Proj3 {
+    double s, tg;
+};
+__device__ __forceinline__ Proj3 proj3_load(const Step3DArgs &a, int64_t j)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+        a.nsum[(j + 1) % 3] = 0.0;
+        if (j == 0 && a.proj == PROJ_SET) *a.ntarget = a.nsum[0];
+    }
+    return {a.nsum[j % 3], (j == 0 && a.proj == PROJ_SET) ? 0.0 : *a.ntarget};
+}
+__device__ __forceinline__ float proj3_factor(Proj3 p)
+{
+    // the ratio is 1 + O(1e-7): FP32 suffices; C = 1 while recording the target
+    return (p.tg > 0.0 && p.s > 0.0 && isfinite(p.s)) ? sqrtf((float)p.tg / (float)p.s) : 1.0f;
+}
+
+// the transforms of the 3D kernels: plain twiddles with the projection (FP32)
+template <int N, bool INV, int ILV, bool PROJ, int E, typename R>
+__device__ __forceinline__ void fft3(cpx<R> (&v)[E], cpx<R> *sm, int t, const Step3DArgs &a)
+{
+    if constexpr (PROJ && sizeof(R) == 4)
+        FftPlan<N, E>::template run<INV, R, ILV, false, false>(v, sm, t, static_cast<const float2 *>(a.tw2));
+    else
+        FftPlan<N, E>::template run<INV, R, ILV>(v, sm, t,
+                                                 reinterpret_cast<const typename TwOf<R>::type *>(a.tw));
+}
+
+template <typename R, int N, bool PROJ = false>
 __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(const Step3DArgs a, int64_t j)
 {
     using Rec = typename Rec3Of<R>::type;
@@ -130,17 +166,20 @@ __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(c
     const int y = blockIdx.y, x = blockIdx.x * TX + l;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)y * N + x;
-    const auto *tw = reinterpret_cast<const typename TwOf<R>::type *>(a.tw);
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
-    FftPlan<N, E>::template run<false, R, TX>(v, sm, t, tw);
+    Proj3 pr{0.0, 0.0};
+    if constexpr (PROJ) pr = proj3_load(a, j);
+    fft3<N, false, TX, PROJ>(v, sm, t, a);
+    R C = R(1);
+    if constexpr (PROJ) C = (R)proj3_factor(pr);
     {
         const Rec rc = reinterpret_cast<const Rec *>(a.rec)[j];
         const int mx = (x < N / 2) ? x : x - N;
         const int my = (y < N / 2) ? y : y - N;
         const R txy = turns_q(mx, rc.g[0], rc.glo[0]) + turns_q(my, rc.g[1], rc.glo[1]);
-        const R scale = R(1) / (R(N) * R(N) * R(N));
+        const R scale = C / (R(N) * R(N) * R(N));
         if constexpr (sizeof(R) == 4) {
             // points in pairs, the phase arithmetic in packed FP32 (bit-identical)
 #pragma unroll
@@ -160,7 +199,7 @@ __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(c
             }
         }
     }
-    FftPlan<N, E>::template run<true, R, TX>(v, sm, t, tw);
+    fft3<N, true, TX, PROJ>(v, sm, t, a);
 #pragma unroll
     for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N * N] = v[e];
 }
@@ -189,7 +228,8 @@ template <int N, int TX> __device__ __forceinline__ void first_pass_exchange(cpx
     __syncthreads();
 }
 
-template <int N> __global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(const Step3DArgs a, int64_t j)
+template <int N, bool PROJ = false>
+__global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(const Step3DArgs a, int64_t j)
 {
     using GEO = Geo3<N>;
     constexpr int E = GEO::E, T = GEO::T, TX = GEO::TX;
@@ -214,6 +254,8 @@ template <int N> __global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(co
     cpx<float> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
+    Proj3 pr{0.0, 0.0};
+    if constexpr (PROJ) pr = proj3_load(a, j);
     bool ok = tc::dft16<false>(v, st);
     first_pass_exchange<N, TX>(v, sm, t);
     stockham_pass<N, E, N / 16, 16, false, true, TX, false>(v, sm, t, tw, 0);
@@ -222,7 +264,7 @@ template <int N> __global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(co
         const int mx = (x < N / 2) ? x : x - N;
         const int my = (y < N / 2) ? y : y - N;
         const float txy = turns_q(mx, rc.g[0], rc.glo[0]) + turns_q(my, rc.g[1], rc.glo[1]);
-        const float scale = 1.0f / ((float)N * (float)N * (float)N);
+        const float scale = (PROJ ? proj3_factor(pr) : 1.0f) / ((float)N * (float)N * (float)N);
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
             const int kz0 = t + T * e, kz1 = kz0 + T;
@@ -258,7 +300,8 @@ constexpr int kPlaneN = 128, kPlaneRow = kPlaneN + kPlaneN / 16, kPlaneThreads =
 
 // VI: the instance's perturbation kind, a template parameter so that the
 // phase loop carries no per-point test of it
-template <int MODE, int VI>
+// PROJ: plain twiddles and the norm sum of the x-phase (proj3_factor)
+template <int MODE, int VI, bool PROJ = false>
 __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, int64_t j)
 {
     constexpr int N = kPlaneN, E = 16, T = N / E, LINES = kPlaneThreads / T;  // 64 lines per round
@@ -273,7 +316,6 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
     }
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
-    const auto *tw = reinterpret_cast<const float4 *>(a.tw);
     // With the inverse y-transform the columns come straight from global
     // memory (lanes are adjacent x: coalesced); otherwise the plane is loaded
     // into shared memory (row y, padded slot of x) by asynchronous 8-byte
@@ -295,12 +337,14 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
             cpx<float> *col = pl + spad(x);
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = psi[(t + T * e) * N + x];
-            FftPlan<N, E>::template run<true, float, kPlaneRow>(v, col, t, tw);
+            fft3<N, true, kPlaneRow, PROJ>(v, col, t, a);
 #pragma unroll
             for (int e = 0; e < E; ++e) col[(t + T * e) * kPlaneRow] = v[e];
             __syncthreads();
         }
     }
+    float dsum = 0.0f;  // this thread's sum of |u|^2 in the x-phase (projection)
+    __shared__ float s_red[kPlaneThreads / 32];
     if constexpr ((MODE & P_INV_X) || (MODE & P_PHASE) || (MODE & P_FWD_X)) {
         const int g = threadIdx.x / T, t = threadIdx.x - g * T;
         const DevInst &ip = *a.inst;
@@ -316,7 +360,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = row[spad(t + T * e)];
             __syncthreads();
-            if constexpr (MODE & P_INV_X) FftPlan<N, E>::template run<true, float>(v, row, t, tw);
+            if constexpr (MODE & P_INV_X) fft3<N, true, 1, PROJ>(v, row, t, a);
             if constexpr (MODE & P_PHASE) {
                 const int my = y - N / 2;
                 const float tyz = turns_q(my, rc.k2[1], rc.k2lo[1]) + tz;
@@ -325,6 +369,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
                 const float evyz = eps * vyz;
                 auto Fof = [&](const cpx<float> &u, int mx) {
                     const float dens = u.x * u.x + u.y * u.y;
+                    if constexpr (PROJ) dsum += dens;
                     return sig * dens + (s_vx[mx + N / 2] + evyz);
                 };
 #pragma unroll
@@ -337,10 +382,28 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
                     apply_turns2(v[e], v[e + 1], turns, 1.0f);
                 }
             }
-            if constexpr (MODE & P_FWD_X) FftPlan<N, E>::template run<false, float>(v, row, t, tw);
+            if constexpr (MODE & P_FWD_X) fft3<N, false, 1, PROJ>(v, row, t, a);
 #pragma unroll
             for (int e = 0; e < E; ++e) row[spad(t + T * e)] = v[e];
+            if constexpr (PROJ && (MODE & P_PHASE)) {
+                if (r == N / LINES - 1) {
+                    // the plane's sum of |u|^2: warp sums here, published by
+                    // the barrier below, added by one thread into slot j mod 3
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = dsum;
+                }
+            }
             __syncthreads();
+        }
+        if constexpr (PROJ && (MODE & P_PHASE)) {
+            if (threadIdx.x < 32) {
+                // the sixteen warp sums in FP32, the planes' totals in FP64
+                float w = threadIdx.x < kPlaneThreads / 32 ? s_red[threadIdx.x] : 0.0f;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                if (threadIdx.x == 0) atomicAdd(a.nsum + (j % 3), (double)w);
+            }
         }
     }
     bool bad = false;
@@ -353,7 +416,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = col[(t + T * e) * kPlaneRow];
             __syncthreads();
-            FftPlan<N, E>::template run<false, float, kPlaneRow>(v, col, t, tw);
+            fft3<N, false, kPlaneRow, PROJ>(v, col, t, a);
 #pragma unroll
             for (int e = 0; e < E; ++e) psi[(t + T * e) * N + x] = v[e];
         }
@@ -540,7 +603,7 @@ template <typename R, int N> static cudaError_t diag3d(const Diag3DArgs &a, cuda
     return cudaGetLastError();
 }
 
-template <int VI> static cudaError_t run3d_plane_vi(const Step3DArgs &a, cudaStream_t st)
+template <int VI, bool PROJ> static cudaError_t run3d_plane_vi(const Step3DArgs &a, cudaStream_t st)
 {
     constexpr int N = kPlaneN;
     using GEO = Geo3<N>;
@@ -550,30 +613,32 @@ template <int VI> static cudaError_t run3d_plane_vi(const Step3DArgs &a, cudaStr
     static bool prepared = false;
     if (!prepared) {
         cudaError_t e;
-        if ((e = allow_smem(plane3d<FIRST, VI>, ps)) != cudaSuccess) return e;
-        if ((e = allow_smem(plane3d<MID, VI>, ps)) != cudaSuccess) return e;
-        if ((e = allow_smem(plane3d<LAST, VI>, ps)) != cudaSuccess) return e;
-        if ((e = allow_smem(zpass3d<float, N>, ts)) != cudaSuccess) return e;
-        if ((e = allow_smem(zpass3d_tc<N>, zpass_tc_smem<N>())) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<FIRST, VI, PROJ>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<MID, VI, PROJ>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(plane3d<LAST, VI, PROJ>, ps)) != cudaSuccess) return e;
+        if ((e = allow_smem(zpass3d<float, N, PROJ>, ts)) != cudaSuccess) return e;
+        if ((e = allow_smem(zpass3d_tc<N, PROJ>, zpass_tc_smem<N>())) != cudaSuccess) return e;
         prepared = true;
     }
     const dim3 tg(N / GEO::TX, N);
-    plane3d<FIRST, VI><<<N, kPlaneThreads, ps, st>>>(a, 0);
+    plane3d<FIRST, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, 0);
     for (int64_t j = 0; j < a.nstage; ++j) {
-        if (a.dft_tc) zpass3d_tc<N><<<tg, GEO::TT, zpass_tc_smem<N>(), st>>>(a, j);
-        else zpass3d<float, N><<<tg, GEO::TT, ts, st>>>(a, j);
-        if (j + 1 < a.nstage) plane3d<MID, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
-        else plane3d<LAST, VI><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+        if (a.dft_tc) zpass3d_tc<N, PROJ><<<tg, GEO::TT, zpass_tc_smem<N>(), st>>>(a, j);
+        else zpass3d<float, N, PROJ><<<tg, GEO::TT, ts, st>>>(a, j);
+        if (j + 1 < a.nstage) plane3d<MID, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+        else plane3d<LAST, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
     }
     return cudaGetLastError();
 }
 
 static cudaError_t run3d_plane(const Step3DArgs &a, cudaStream_t st)
 {
+    const bool proj = a.proj != PROJ_OFF;
     switch (a.vi) {
-    case HFS_VI_COS: return run3d_plane_vi<HFS_VI_COS>(a, st);
-    case HFS_VI_X4: return run3d_plane_vi<HFS_VI_X4>(a, st);
-    case HFS_VI_NONE: return run3d_plane_vi<HFS_VI_NONE>(a, st);
+    case HFS_VI_COS: return proj ? run3d_plane_vi<HFS_VI_COS, true>(a, st) : run3d_plane_vi<HFS_VI_COS, false>(a, st);
+    case HFS_VI_X4: return proj ? run3d_plane_vi<HFS_VI_X4, true>(a, st) : run3d_plane_vi<HFS_VI_X4, false>(a, st);
+    case HFS_VI_NONE:
+        return proj ? run3d_plane_vi<HFS_VI_NONE, true>(a, st) : run3d_plane_vi<HFS_VI_NONE, false>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -16,6 +16,13 @@ struct Step3DArgs {
     int n;   // points per axis
     int vi;  // perturbation kind in effect (HFS_VI_NONE where eps = 0)
     int dft_tc;  // complex64, n = 64 / 128: first z-pass radix-16 stages on the tensor cores
+    // norm projection (complex64, n = 128): plain FP32 twiddles (float2), the
+    // per-sub-stage sums of |u|^2 (three FP64 slots, zeroed by the host at
+    // each chunk start), the call's target sum, PROJ_OFF / PROJ_SET / PROJ_USE
+    const void *tw2;
+    double *nsum;
+    double *ntarget;
+    int proj;
 };
 
 struct Diag3DArgs {
