@@ -49,12 +49,8 @@ PLAN_CACHE = os.path.join(ROOT, "paper_1007_3470_gb300", "tuned_plans.json")
 def tune(solver, trial_steps):
     """Plans from the cache, or the search (recorded in the cache when the file
     is writable); returns (plans, how they were obtained)."""
-    from paper_1007_3470_gb300 import hfs
-    try:
-        plans = solver.autotune(trial_steps, cache=PLAN_CACHE)
-        return plans, {"cache": os.path.relpath(PLAN_CACHE, ROOT), "hit": solver.tune_cache_hit}
-    except hfs.HfsError:
-        return solver.autotune(trial_steps), {"cache": None, "hit": False}
+    plans = solver.autotune(trial_steps, cache=PLAN_CACHE)
+    return plans, {"cache": os.path.relpath(PLAN_CACHE, ROOT), "hit": solver.tune_cache_hit}
 
 
 # DRAM bytes per launch of the fused step kernel (dram__bytes_read.sum +

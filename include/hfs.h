@@ -256,10 +256,10 @@ int hfs_autotune(hfs_ctx_t ctx, int trial_steps, int32_t *best_plans);
  * library's sources, the perturbation-kind variant, the norm projection, the
  * mode, the schedule (flow, split, stages) and the batch's count of
  * instances per grid size.  A matching entry is applied without timing
- * anything (*hit = 1); otherwise the search runs and its result is added to
- * the file (*hit = 0; the file is written to path.tmp and renamed).
- * Errors: as hfs_autotune; HFS_ERR_INVALID_ARG when the file cannot be
- * written. */
+ * anything (*hit = 1); otherwise the search runs, its plans take effect and
+ * its result is added to the file (*hit = 0; written to path.tmp and renamed;
+ * a file that cannot be written is left as it is).
+ * Errors: as hfs_autotune. */
 int hfs_autotune_cache(hfs_ctx_t ctx, const char *path, int trial_steps, int32_t *best_plans, int *hit);
 
 /* ---- profiling -------------------------------------------------------- */

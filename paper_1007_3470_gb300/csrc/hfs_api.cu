@@ -1101,7 +1101,8 @@ int hfs_autotune_cache(hfs_ctx_t c, const char *path, int trial_steps, int32_t *
             replaced = true;
         }
     if (!replaced) entries.push_back(e);
-    if (!write_cache(path, entries)) return HFS_ERR_INVALID_ARG;
+    // a cache that cannot be written leaves the tuned plans in effect
+    (void)write_cache(path, entries);
     if (best_plans) std::copy(e.plans, e.plans + kNumSizes, best_plans);
     if (hit) *hit = 0;
     return HFS_OK;

@@ -106,3 +106,20 @@ def test_plan_validation():
             d.set_plan(256, p)
     d.set_plan(256, 8)
     d.close()
+
+
+def test_autotune_cache_unwritable_path_still_tunes(tmp_path):
+    need_gpu()
+    from paper_1007_3470_gb300 import hfs
+    insts, psis, _ = W.batch_1d(count=64, seed=14)
+    path = str(tmp_path / "missing_dir" / "plans.json")
+    s = hfs.Solver(insts, precision="c64", chunk_steps=8)
+    s.set_schedule(0.005, "strang", hfs.HFS_FLOW_CF4)
+    plans = s.autotune(4, cache=path)
+    assert not s.tune_cache_hit and any(plans)
+    s.set_psi(psis)
+    s.step(8)
+    assert s.status() == hfs.HFS_OK
+    s.close()
+    import os
+    assert not os.path.exists(path)
