@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "hfs.h"
 
 namespace hfs {
@@ -74,7 +76,23 @@ struct DevInst {
     double law[3];
     double axis_scale[3];
     double eps, vi_k, sigma;
+    // 1D, V_I = cos(k x): k x / (2 pi) in turns as (a_hi + a_lo) + (b_hi + b_lo) m
+    // for x = xc + m dx (a = k xc / (2 pi) mod 1, b = k dx / (2 pi)), FP32 pairs
+    float vi_turns[4];
 };
+
+// vi_turns of a 1D instance from its FP64 parameters (host)
+inline void set_vi_turns(DevInst &d)
+{
+    const double inv_2pi = 0.159154943091895335768883763372514362;
+    const double b = d.vi_k * d.dx[0] * inv_2pi;
+    double a = d.vi_k * d.xc[0] * inv_2pi;
+    a -= std::nearbyint(a);
+    d.vi_turns[0] = (float)b;
+    d.vi_turns[1] = (float)(b - (double)d.vi_turns[0]);
+    d.vi_turns[2] = (float)a;
+    d.vi_turns[3] = (float)(a - (double)d.vi_turns[2]);
+}
 
 // FSAL-merged record of sub-stage j (FP32 path, 32 bytes):
 //   x-phase X_j :  turns(x) = K2 m^2 + K1 m + K0   with m = j - n/2

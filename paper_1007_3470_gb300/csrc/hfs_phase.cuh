@@ -95,6 +95,24 @@ __device__ __forceinline__ cpx<float> apply_turns(cpx<float> u, float turns, flo
     return finish_rotation(u, __float_as_int(tq) & 3, sn * scale, cm1 * scale, scale);
 }
 
+// cos and sin of 2 pi (r + c) for an exact reduced part |r| <= 1/2 and a
+// small correction c: the quarter turn split off as in apply_turns, the
+// remainder through small_rotation, then the quarter turn applied exactly
+// (cos(a + q pi/2), sin(a + q pi/2) are +-cos a, +-sin a).
+__device__ __forceinline__ void sincos_turns(float r, float c, float &cs, float &sn)
+{
+    const float tq = fmaf(4.0f, r + c, kRoundMagic);
+    const float q = tq - kRoundMagic;
+    float s, cm1;
+    small_rotation(fmaf(q, -0.25f, r) + c, s, cm1);
+    const float co = 1.0f + cm1;
+    const int qi = __float_as_int(tq) & 3;
+    const float a = (qi & 1) ? s : co;  // cos or sin of the remainder
+    const float b = (qi & 1) ? co : s;
+    cs = (qi == 1 || qi == 2) ? -a : a;
+    sn = (qi >= 2) ? -b : b;
+}
+
 // The merged phases of a pair of grid points, in turns, as an exact part r
 // (the reduced product hi m2 - rint(hi m2), |r| <= 1/2) plus a correction c
 // (the product's rounding error, lo m2 and any further terms).  The angle is

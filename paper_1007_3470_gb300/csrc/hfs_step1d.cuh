@@ -33,6 +33,7 @@ template <typename R> struct TeamParams {
     R xc, dx, eps, vik, sigma;
     int vikind;
     bool asym;
+    float vt_b[2], vt_a[2];  // V_I = cos(k x) in turns (DevInst::vi_turns)
 };
 
 template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const DevInst &p)
@@ -45,6 +46,10 @@ template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const
     tp.sigma = (R)p.sigma;
     tp.vikind = (p.eps != 0.0) ? p.vi_kind : HFS_VI_NONE;
     tp.asym = (p.xc[0] != 0.0);
+    tp.vt_b[0] = p.vi_turns[0];
+    tp.vt_b[1] = p.vi_turns[1];
+    tp.vt_a[0] = p.vi_turns[2];
+    tp.vt_a[1] = p.vi_turns[3];
     return tp;
 }
 
@@ -77,12 +82,57 @@ template <int E> __device__ __forceinline__ void fence_group(cpx<double> (&v)[E]
 }
 
 // merged x-phase X_j on the register layout (position t + T e)
-// eps V_I(x) at a thread's own grid points (VI = -1: the instance's kind,
-// zero when eps = 0; VI >= 0: the launch's kind on a box symmetric about 0)
-template <int VI> __device__ __forceinline__ float eps_vi(float mf, const TeamParams<float> &tp)
+// The table vt of eps V_I at a thread's points m = t + T e - N/2 (VI = -1:
+// the instance's kind, none when eps = 0; VI >= 0: the launch's kind on a
+// box symmetric about 0).  For
+// V_I = cos(k x) the phase exp(2 pi i k x_m) is formed in turns, (a + b m)
+// mod 1 with the exact product reduction of frac_turns, at e = 0, then
+// advanced E - 1 times by the constant factor exp(2 pi i b T) (b T is exact:
+// T is a power of two).  Each product adds about one rounding, so the table
+// is within a few E units of FP32 rounding of cos(k x) whatever the size of
+// k x, at E - 1 complex products and two small rotations per thread instead
+// of E calls of cosf (whose inlined reductions also crowd the instruction
+// cache when the table is rebuilt every launch, as in the streaming mode).
+template <int N, int E, int VI>
+__device__ __forceinline__ void vi_table(float *vt, int t, const TeamParams<float> &tp)
 {
-    const float x = VI < 0 ? fmaf(mf, tp.dx, tp.xc) : mf * tp.dx;
-    return tp.eps * vi_eval(VI < 0 ? tp.vikind : VI, x, tp.vik);
+    constexpr int T = N / E;
+    const int kind = VI < 0 ? tp.vikind : VI;
+    if (kind == HFS_VI_COS) {
+        const float m0 = (float)(t - N / 2);
+        // a + b m0 mod 1 as an exact part r plus a small correction c
+        const float p = tp.vt_b[0] * m0;
+        float r = p - rintf(p);
+        float c = fmaf(tp.vt_b[1], m0, fmaf(tp.vt_b[0], m0, -p));
+        if (VI < 0) {
+            const float s = r + tp.vt_a[0];  // |r|, |a| <= 1/2: two-sum, then re-reduce
+            const float bb = s - r;
+            c += (r - (s - bb)) + (tp.vt_a[0] - bb) + tp.vt_a[1];
+            r = s - rintf(s);
+        }
+        float zc, zs, wc, ws;
+        sincos_turns(r, c, zc, zs);
+        const float pw = tp.vt_b[0] * (float)T;
+        sincos_turns(pw - rintf(pw), tp.vt_b[1] * (float)T, wc, ws);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            vt[t + T * e] = tp.eps * zc;
+            const float nc = fmaf(zc, wc, -zs * ws);
+            zs = fmaf(zs, wc, zc * ws);
+            zc = nc;
+        }
+    } else if (kind == HFS_VI_X4) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float mf = (float)(t + T * e - N / 2);
+            const float x = VI < 0 ? fmaf(mf, tp.dx, tp.xc) : mf * tp.dx;
+            const float x2 = x * x;
+            vt[t + T * e] = tp.eps * (x2 * x2);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) vt[t + T * e] = 0.0f;
+    }
 }
 
 // VI >= 0: every instance of the launch has the perturbation kind VI and a
@@ -299,10 +349,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
     // reads back only the entries it wrote), then the norm-sum slots
     float *vt = reinterpret_cast<float *>(smem + step1d_exchange_elems) + g * N;
     float *slots = reinterpret_cast<float *>(smem + step1d_exchange_elems) + step1d_vtable_floats;
-    if constexpr (sizeof(R) == 4 && VI != HFS_VI_NONE) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) vt[t + T * e] = eps_vi<VI>((float)(t + T * e - N / 2), tp);
-    }
+    if constexpr (sizeof(R) == 4 && VI != HFS_VI_NONE) vi_table<N, E, VI>(vt, t, tp);
     step_loop<R, VI, N, E, ALT, PROJ && sizeof(R) == 4>(a, v, t, g, active, idx, rec, tp, sm, tw, vt, slots);
     if (a.final_x) {
         const Rec rc = rec[a.j1];
