@@ -195,6 +195,25 @@ int hfs_set_dft_engine(hfs_ctx_t ctx, int engine);
  * HFS_ERR_INVALID_ARG when graphs are enabled and the stream is NULL. */
 int hfs_set_graphs(hfs_ctx_t ctx, int enable);
 
+/* Schedule reuse for 1D contexts (enable != 0; default off).  The phase
+ * records of a call (the FP64 stage flows of Lemma 2 / Theorems 1-2 merged
+ * as in Eq. prod-genHarmOsc) depend only on the call's start time, its step
+ * count and the schedule, so with reuse on the context keeps two record
+ * buffers, each tagged with the call it holds: a call of at most one chunk
+ * whose records are held skips the FP64 schedule kernels, and each call
+ * computes the records of the call that would follow it (start time
+ * t + nsteps dt) on an internal stream, in parallel with its fused step
+ * kernel, which it launches at the device's highest scheduling priority so
+ * that the schedule fills only the SMs that the step kernel leaves.  The
+ * records, and so the results, are bit-identical to those computed in line.
+ * Any change of schedule, instances, plans, stream or buffers drops the held
+ * records.  The second buffer enlarges the workspace (hfs_workspace_size
+ * reports the size with the current setting): when the bound workspace is too
+ * small the context is left unbound and HFS_ERR_WORKSPACE is returned; bind
+ * again with a workspace of the new size.
+ * Errors: HFS_ERR_UNSUPPORTED (3D), HFS_ERR_WORKSPACE, HFS_ERR_CUDA. */
+int hfs_set_schedule_reuse(hfs_ctx_t ctx, int enable);
+
 /* Current time t_n (host copy; advanced by hfs_step). */
 int hfs_set_time(hfs_ctx_t ctx, double t);
 int hfs_get_time(hfs_ctx_t ctx, double *t);

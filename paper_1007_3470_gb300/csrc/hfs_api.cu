@@ -95,7 +95,7 @@ double omega_bound(const hfs_instance &p, double t0, double t1)
 namespace {
 
 struct Layout {
-    size_t status, ticket, tdev, inst, order, work, twf, twd, twp, fge, nodes, rec, diag, norm, nsum3, total;
+    size_t status, ticket, tdev, inst, order, work, twf, twd, twp, fge, nodes, rec, diag, norm, nsum3, rec2, total;
 };
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -141,13 +141,28 @@ struct hfs_ctx_s {
     Layout lay{};
     double t = 0.0;
     int sm_count = 0;
-    // graph cache keyed by nsteps
+    // graph cache keyed by graph_key (steps per call and schedule-reuse plan)
     std::map<int64_t, cudaGraphExec_t> graphs_by_n;
     uint64_t version = 0;  // bumps invalidate cached graphs
     std::vector<double> diag_host;
     // profiling events around the fused step kernels
     bool profiling = false, prof_valid = false;
     cudaEvent_t kev[2] = {nullptr, nullptr};
+    // 1D schedule reuse (hfs_set_schedule_reuse): two record buffers, each
+    // tagged with the call it holds (start time, steps, context version); the
+    // next call's records are computed on an auxiliary stream, in a branch
+    // parallel to the step kernel, which is launched at the highest priority
+    struct RecSlot {
+        bool valid = false;
+        double t0 = 0.0;
+        int64_t nsteps = 0;
+        uint64_t version = 0;
+    };
+    bool sched_reuse = false;
+    RecSlot slot[2];
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    int prio_high = 0;
 };
 
 namespace {
@@ -198,6 +213,9 @@ Layout make_layout(const hfs_ctx_s *c, int64_t chunk)
     L.diag = take(sizeof(double) * 2 * std::max<int64_t>(c->count, 1));
     L.norm = take(sizeof(float) * std::max<int64_t>(c->count, 1));
     L.nsum3 = take(4 * sizeof(double));  // 3D projection: three sum slots and the target
+    // the second record buffer of the schedule reuse, last so that the other
+    // offsets do not depend on it
+    L.rec2 = (c->sched_reuse && c->dim == 1) ? take(recsz * c->count * (nstage + 1)) : 0;
     L.total = o;
     return L;
 }
@@ -263,6 +281,45 @@ void drop_graphs(hfs_ctx_s *c)
     c->version++;
 }
 
+// what one hfs_step() call does with the record buffers under schedule reuse:
+// cur holds (or, with compute, receives) the records of this call; with
+// prefetch the next call's records (start time t + nsteps h) go to nxt
+struct ReusePlan {
+    bool on = false, compute = true, prefetch = false;
+    int cur = 0, nxt = 1;
+};
+
+ReusePlan plan_reuse(const hfs_ctx_s *c, int64_t nsteps)
+{
+    ReusePlan p;
+    if (!(c->dim == 1 && c->sched_reuse && c->lay.rec2 != 0 && nsteps <= c->chunk)) return p;
+    p.on = true;
+    auto holds = [&](int k, double t0) {
+        const hfs_ctx_s::RecSlot &r = c->slot[k];
+        return r.valid && r.version == c->version && r.nsteps == nsteps && r.t0 == t0;
+    };
+    const double t1 = c->t + (double)nsteps * c->sc.h;
+    p.cur = holds(0, c->t) ? 0 : holds(1, c->t) ? 1 : -1;
+    p.compute = p.cur < 0;
+    if (p.compute) p.cur = holds(0, t1) ? 1 : 0;  // keep a buffer that holds the next call's records
+    p.nxt = 1 - p.cur;
+    p.prefetch = !holds(p.nxt, t1);
+    return p;
+}
+
+void commit_reuse(hfs_ctx_s *c, const ReusePlan &p, int64_t nsteps)
+{
+    if (!p.on) return;
+    c->slot[p.cur] = {true, c->t, nsteps, c->version};
+    if (p.prefetch) c->slot[p.nxt] = {true, c->t + (double)nsteps * c->sc.h, nsteps, c->version};
+}
+
+// graph cache key: the step count and the reuse plan
+int64_t graph_key(int64_t nsteps, const ReusePlan &p)
+{
+    return nsteps * 16 + (p.on ? (p.cur * 4 + (p.compute ? 2 : 0) + (p.prefetch ? 1 : 0)) : 8);
+}
+
 int check_validity(const hfs_ctx_s *c, int64_t nsteps)
 {
     if (c->sc.split != HFS_SPLIT_HO) return HFS_OK;
@@ -297,8 +354,9 @@ int step_grid(const hfs_ctx_s *c, bool wide)
     return std::max(1, std::min<int>((int)c->work.size(), c->sm_count * per_sm));
 }
 
-// enqueue nsteps steps (no graph logic); work list already uploaded
-int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
+// enqueue nsteps steps (no graph logic); work list already uploaded; rp:
+// the schedule-reuse plan of the call (plan_reuse; off by default)
+int enqueue_steps(hfs_ctx_s *c, int64_t nsteps, const ReusePlan &rp = ReusePlan())
 {
     (void)cudaGetLastError();  // a failed earlier runtime call must not be reported by the launches below
     const bool fp64 = c->precision == HFS_C128;
@@ -314,24 +372,45 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
         const int64_t S = std::min(c->chunk, nsteps - done);
         const int64_t nstage = S * m;
         const double toff = (double)done * c->sc.h;
-        if (c->sc.split == HFS_SPLIT_HO)
-            CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, toff, nstage, c->law, c->law_shared,
-                                 wptr<void>(c, c->lay.nodes), fge, status, c->stream));
+        // the FP64 schedule of sub-stages from time t + t_off into record buffer r
+        auto schedule = [&](cudaStream_t st, double t_off, void *r) -> int {
+            if (c->sc.split == HFS_SPLIT_HO)
+                CK(launch_stage_flow(dinst, c->count, c->dim, c->sc, tdev, t_off, nstage, c->law, c->law_shared,
+                                     wptr<void>(c, c->lay.nodes), fge, status, st));
+            if (c->dim == 1) CK(launch_records1d(fp64, dinst, c->count, c->sc, tdev, t_off, nstage, fge, r, status, st));
+            else CK(launch_records3d(fp64, dinst, c->sc, tdev, t_off, nstage, fge, r, status, st));
+            return HFS_OK;
+        };
+        // under schedule reuse a call is one chunk (done = 0, S = nsteps)
+        void *rec_now = (rp.on && rp.cur == 1) ? wptr<void>(c, c->lay.rec2) : rec;
+        if (!rp.on || rp.compute) {
+            const int s = schedule(c->stream, toff, rec_now);
+            if (s) return s;
+        }
+        if (rp.on && rp.prefetch) {
+            // the next call's records, parallel to the step kernel
+            void *rec_next = rp.nxt == 1 ? wptr<void>(c, c->lay.rec2) : rec;
+            CK(cudaEventRecord(c->fork_ev, c->stream));
+            CK(cudaStreamWaitEvent(c->aux, c->fork_ev, 0));
+            const int s = schedule(c->aux, (double)nsteps * c->sc.h, rec_next);
+            if (s) return s;
+            CK(cudaEventRecord(c->join_ev, c->aux));
+        }
         if (c->dim == 1) {
-            CK(launch_records1d(fp64, dinst, c->count, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
             Step1DArgs a{};
             a.psi = c->psi;
             a.inst = dinst;
             a.order = wptr<int32_t>(c, c->lay.order);
             a.work = wptr<WorkItem>(c, c->lay.work);
             a.nwork = (int32_t)c->work.size();
-            a.rec = rec;
+            a.rec = rec_now;
             a.nrec = nstage + 1;
             a.tw = fp64 ? wptr<void>(c, c->lay.twd) : wptr<void>(c, c->lay.twf);
             a.ticket = ticket;
             a.status = status;
             a.norm_target = wptr<float>(c, c->lay.norm);
             a.tw2 = wptr<void>(c, c->lay.twp);
+            a.streaming = c->mode != HFS_MODE_RESIDENT ? 1 : 0;
             const bool wide = worklist_wide(c);
             const int grid = step_grid(c, wide);
             const int64_t per = (c->mode == HFS_MODE_RESIDENT) ? S : std::max(1, c->spl);
@@ -344,11 +423,11 @@ int enqueue_steps(hfs_ctx_s *c, int64_t nsteps)
                 // the first launch of the call records the norm it projects onto
                 a.proj = !c->norm_projection ? PROJ_OFF : (done == 0 && s0 == 0) ? PROJ_SET : PROJ_USE;
                 CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->stream));
-                CK(launch_step1d(fp64, c->variant, a, grid, c->stream, wide));
+                CK(launch_step1d(fp64, c->variant, a, grid, c->stream, wide, rp.prefetch ? c->prio_high : 0));
             }
+            if (rp.on && rp.prefetch) CK(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
             if (c->profiling && done + S >= nsteps) CK(record_prof(c, 1));
         } else {
-            CK(launch_records3d(fp64, dinst, c->sc, tdev, toff, nstage, fge, rec, status, c->stream));
             Step3DArgs a{};
             a.psi = c->psi;
             a.inst = dinst;
@@ -492,6 +571,9 @@ void hfs_destroy(hfs_ctx_t c)
     if (!c) return;
     drop_graphs(c);
     drop_events(c);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
 
@@ -650,6 +732,35 @@ int hfs_set_dft_engine(hfs_ctx_t c, int engine)
     return HFS_OK;
 }
 
+int hfs_set_schedule_reuse(hfs_ctx_t c, int enable)
+{
+    if (!c) return HFS_ERR_INVALID_ARG;
+    if (c->dim != 1) return enable ? HFS_ERR_UNSUPPORTED : HFS_OK;
+    if (enable && !c->aux) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        c->prio_high = greatest;
+        CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    drop_graphs(c);
+    c->slot[0] = c->slot[1] = hfs_ctx_s::RecSlot{};
+    c->sched_reuse = enable != 0;
+    if (c->work_base) {
+        const Layout L = make_layout(c, c->chunk);
+        if (L.total > c->work_bytes) {
+            // the bound workspace has no room for the second record buffer
+            c->psi = nullptr;
+            c->work_base = nullptr;
+            c->work_bytes = 0;
+            return HFS_ERR_WORKSPACE;
+        }
+        c->lay = L;
+    }
+    return HFS_OK;
+}
+
 int hfs_set_graphs(hfs_ctx_t c, int enable)
 {
     if (!c) return HFS_ERR_INVALID_ARG;
@@ -708,13 +819,15 @@ int hfs_step(hfs_ctx_t c, int64_t nsteps)
     if (make_layout(c, c->chunk).total > c->work_bytes) return HFS_ERR_WORKSPACE;
     s = check_validity(c, nsteps);
     if (s) return s;
+    const ReusePlan rp = plan_reuse(c, nsteps);
     if (c->graphs) {
         if (c->stream == nullptr) return HFS_ERR_INVALID_ARG;  // the legacy stream cannot be captured
-        auto it = c->graphs_by_n.find(nsteps);
+        const int64_t key = graph_key(nsteps, rp);
+        auto it = c->graphs_by_n.find(key);
         if (it == c->graphs_by_n.end()) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            s = enqueue_steps(c, nsteps);
+            s = enqueue_steps(c, nsteps, rp);
             cudaError_t e = cudaStreamEndCapture(c->stream, &g);
             if (s) {
                 if (g) cudaGraphDestroy(g);
@@ -722,16 +835,20 @@ int hfs_step(hfs_ctx_t c, int64_t nsteps)
             }
             CK(e);
             cudaGraphExec_t ge = nullptr;
-            e = cudaGraphInstantiate(&ge, g, 0);
+            // per-node priorities: the step kernel's launch priority survives capture
+            e = cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(g);
             CK(e);
-            it = c->graphs_by_n.emplace(nsteps, ge).first;
+            it = c->graphs_by_n.emplace(key, ge).first;
         }
         CK(cudaGraphLaunch(it->second, c->stream));
     } else {
-        s = enqueue_steps(c, nsteps);
+        s = enqueue_steps(c, nsteps, rp);
         if (s) return s;
     }
+    // record buffer 0 is the one a call without reuse writes
+    if (rp.on) commit_reuse(c, rp, nsteps);
+    else c->slot[0].valid = false;
     c->t += (double)nsteps * c->sc.h;
     if (c->profiling) c->prof_valid = true;
     return HFS_OK;

@@ -63,12 +63,15 @@ struct Step1DArgs {
     const void *tw2;                // plain FP32 twiddle table (float2), read with the norm projection
     float *norm_target;             // per instance: target sum |u|^2 of the norm projection
     int32_t proj;                   // PROJ_OFF, PROJ_SET (first launch of a call), PROJ_USE
+    int32_t streaming;              // fewer sub-stages per launch than the chunk holds (streaming mode)
 };
 enum : int32_t { PROJ_OFF = 0, PROJ_SET = 1, PROJ_USE = 2 };
 // variant: HFS_VI_* when every instance has that perturbation kind and a box
 // symmetric about 0 (FP32 only; from step1d_variant), -1 for the generic kernel
 // wide: the work list holds plans of the wide set (plan_is_wide; FP32 only)
-cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st, bool wide = false);
+// priority: scheduling priority of the launch (0: the stream's)
+cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st, bool wide = false,
+                          int priority = 0);
 int step1d_ctas_per_sm(bool fp64, int variant, bool wide = false);
 int step1d_variant(const hfs_instance *inst, int64_t count);
 size_t step1d_smem_bytes(bool fp64);

@@ -170,20 +170,22 @@ int step1d_ctas_per_sm(bool fp64, int variant, bool wide)
     return wide ? ctas_per_sm_f<true>(variant) : ctas_per_sm_f<false>(variant);
 }
 
-template <bool WIDE> static cudaError_t launch_f(int variant, const Step1DArgs &a, int grid, cudaStream_t st)
+template <bool WIDE>
+static cudaError_t launch_f(int variant, const Step1DArgs &a, int grid, cudaStream_t st, int prio)
 {
     switch (variant) {
-    case HFS_VI_NONE: return step1d_launch_t<float, HFS_VI_NONE, WIDE>(a, grid, st);
-    case HFS_VI_X4: return step1d_launch_t<float, HFS_VI_X4, WIDE>(a, grid, st);
-    case HFS_VI_COS: return step1d_launch_t<float, HFS_VI_COS, WIDE>(a, grid, st);
-    default: return step1d_launch_t<float, -1, WIDE>(a, grid, st);
+    case HFS_VI_NONE: return step1d_launch_t<float, HFS_VI_NONE, WIDE>(a, grid, st, prio);
+    case HFS_VI_X4: return step1d_launch_t<float, HFS_VI_X4, WIDE>(a, grid, st, prio);
+    case HFS_VI_COS: return step1d_launch_t<float, HFS_VI_COS, WIDE>(a, grid, st, prio);
+    default: return step1d_launch_t<float, -1, WIDE>(a, grid, st, prio);
     }
 }
 
-cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st, bool wide)
+cudaError_t launch_step1d(bool fp64, int variant, const Step1DArgs &a, int grid, cudaStream_t st, bool wide,
+                          int priority)
 {
-    if (fp64) return wide ? cudaErrorInvalidValue : step1d_launch_t<double, -1, false>(a, grid, st);
-    return wide ? launch_f<true>(variant, a, grid, st) : launch_f<false>(variant, a, grid, st);
+    if (fp64) return wide ? cudaErrorInvalidValue : step1d_launch_t<double, -1, false>(a, grid, st, priority);
+    return wide ? launch_f<true>(variant, a, grid, st, priority) : launch_f<false>(variant, a, grid, st, priority);
 }
 
 int step1d_variant(const hfs_instance *inst, int64_t count)

@@ -326,6 +326,36 @@ __device__ __forceinline__ void step_loop(const Step1DArgs &a, cpx<R> (&v)[E], i
     }
 }
 
+// state loads and stores of streaming launches carry the evict-first hint,
+// so that a state larger than L2 passing through it every step does not push
+// out the kernel's code, tables and phase records
+__device__ __forceinline__ cpx<float> ld_state(const cpx<float> *p, bool streaming)
+{
+    if (streaming) {
+        const float2 f = __ldcs(reinterpret_cast<const float2 *>(p));
+        return {f.x, f.y};
+    }
+    return *p;
+}
+__device__ __forceinline__ cpx<double> ld_state(const cpx<double> *p, bool streaming)
+{
+    if (streaming) {
+        const double2 f = __ldcs(reinterpret_cast<const double2 *>(p));
+        return {f.x, f.y};
+    }
+    return *p;
+}
+__device__ __forceinline__ void st_state(cpx<float> *p, cpx<float> v, bool streaming)
+{
+    if (streaming) __stcs(reinterpret_cast<float2 *>(p), make_float2(v.x, v.y));
+    else *p = v;
+}
+__device__ __forceinline__ void st_state(cpx<double> *p, cpx<double> v, bool streaming)
+{
+    if (streaming) __stcs(reinterpret_cast<double2 *>(p), make_double2(v.x, v.y));
+    else *p = v;
+}
+
 template <typename R, int VI, int N, int E, bool ALT, bool PROJ>
 __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &it, cpx<R> *smem)
 {
@@ -344,7 +374,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
 
     cpx<R> v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = active ? psi[t + T * e] : cpx<R>{R(0), R(0)};
+    for (int e = 0; e < E; ++e) v[e] = active ? ld_state(psi + t + T * e, a.streaming) : cpx<R>{R(0), R(0)};
     // FP32: the table of eps V_I behind the exchange buffers (each thread
     // reads back only the entries it wrote), then the norm-sum slots
     float *vt = reinterpret_cast<float *>(smem + step1d_exchange_elems) + g * N;
@@ -360,7 +390,7 @@ __device__ __forceinline__ void step_item(const Step1DArgs &a, const WorkItem &i
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            psi[t + T * e] = v[e];
+            st_state(psi + t + T * e, v[e], a.streaming);
             bad |= !(isfinite(v[e].x) && isfinite(v[e].y));
         }
         if (bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
@@ -391,11 +421,17 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R> *smem = reinterpret_cast<cpx<R> *>(smem_raw);
     __shared__ int s_item;
+    // streaming launches claim the next item when they start the current one
+    // (the ticket's round trip overlaps the work); resident launches claim
+    // when they need one, so that the long items at the end balance best
+    if (a.streaming && threadIdx.x == 0) s_item = (int)atomicAdd(a.ticket, 1u);
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.ticket, 1u);
+        if (!a.streaming && threadIdx.x == 0) s_item = (int)atomicAdd(a.ticket, 1u);
         __syncthreads();
         const int w = s_item;
         if (w >= a.nwork) break;
+        unsigned next = 0;
+        if (a.streaming && threadIdx.x == 0) next = atomicAdd(a.ticket, 1u);
         const WorkItem it = a.work[w];
         switch (it.plan) {
 #define HFS_CASE(NN, EE, AA)                                                                                      \
@@ -423,6 +459,7 @@ __global__ void __launch_bounds__(kCtaThreads, MinCtas<R>::value) step1d_kernel(
         }
         }
         __syncthreads();
+        if (a.streaming && threadIdx.x == 0) s_item = (int)next;
     }
 }
 
@@ -454,12 +491,30 @@ template <typename R, int VI, bool WIDE> int step1d_ctas_per_sm_t()
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
-template <typename R, int VI, bool WIDE> cudaError_t step1d_launch_t(const Step1DArgs &a, int grid, cudaStream_t st)
+// priority != 0: launched with that scheduling priority (lower = dispatched
+// first), so that its CTAs take the SMs before those of a concurrent branch
+template <typename R, int VI, bool WIDE>
+cudaError_t step1d_launch_t(const Step1DArgs &a, int grid, cudaStream_t st, int priority)
 {
     const cudaError_t e = step1d_prepare_t<R, VI, WIDE>();
     if (e != cudaSuccess) return e;
     const size_t bytes = step1d_smem_bytes(sizeof(R) == 8);
-    if (sizeof(R) == 4 && a.proj != PROJ_OFF) step1d_kernel<R, VI, WIDE, true><<<grid, kCtaThreads, bytes, st>>>(a);
+    const bool proj = sizeof(R) == 4 && a.proj != PROJ_OFF;
+    if (priority != 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kCtaThreads);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributePriority;
+        at[0].val.priority = priority;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return proj ? cudaLaunchKernelEx(&cfg, step1d_kernel<R, VI, WIDE, true>, a)
+                    : cudaLaunchKernelEx(&cfg, step1d_kernel<R, VI, WIDE, false>, a);
+    }
+    if (proj) step1d_kernel<R, VI, WIDE, true><<<grid, kCtaThreads, bytes, st>>>(a);
     else step1d_kernel<R, VI, WIDE, false><<<grid, kCtaThreads, bytes, st>>>(a);
     return cudaGetLastError();
 }
@@ -468,7 +523,7 @@ template <typename R, int VI, bool WIDE> cudaError_t step1d_launch_t(const Step1
 // specialised FP32 kernel per perturbation kind in hfs_step1d_vi*.cu, the
 // wide FP32 kernels in hfs_step1d_wide*.cu
 #define HFS_STEP1D_VARIANT(EXTERN, R, VI, WIDE)                                                                   \
-    EXTERN template cudaError_t step1d_launch_t<R, VI, WIDE>(const Step1DArgs &, int, cudaStream_t);           \
+    EXTERN template cudaError_t step1d_launch_t<R, VI, WIDE>(const Step1DArgs &, int, cudaStream_t, int);           \
     EXTERN template int step1d_ctas_per_sm_t<R, VI, WIDE>();
 
 }  // namespace hfs

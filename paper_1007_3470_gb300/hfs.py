@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhfs.so")
 
 HFS_OK = 0
+HFS_ERR_WORKSPACE = 8
 HFS_C64, HFS_C128 = 0, 1
 HFS_OMEGA_CONST, HFS_OMEGA_SIN, HFS_OMEGA_COS_SQ, HFS_OMEGA_PULSE = 0, 1, 2, 3
 HFS_VI_NONE, HFS_VI_X4, HFS_VI_COS = 0, 1, 2
@@ -35,7 +36,7 @@ COMPOSITIONS = {"strang": HFS_COMP_STRANG, "srkn6_4": HFS_COMP_SRKN6_4, "ni4_82"
 # every symbol include/hfs.h declares
 EXPORTS = ("hfs_create", "hfs_destroy", "hfs_set_stream", "hfs_state_size", "hfs_instance_offset",
            "hfs_workspace_size", "hfs_bind", "hfs_set_schedule", "hfs_set_mode", "hfs_set_norm_projection",
-           "hfs_set_dft_engine", "hfs_set_graphs", "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi",
+           "hfs_set_dft_engine", "hfs_set_graphs", "hfs_set_schedule_reuse", "hfs_set_time", "hfs_get_time", "hfs_set_psi", "hfs_get_psi",
            "hfs_step", "hfs_norm", "hfs_energy", "hfs_sync_status", "hfs_set_plan", "hfs_set_occupancy",
            "hfs_autotune", "hfs_autotune_cache", "hfs_set_profiling", "hfs_last_step_kernel_ms",
            "hfs_step1d_noalloc", "hfs_error_string")
@@ -87,6 +88,7 @@ def lib():
             "hfs_set_mode": [vp, i32, i32],
             "hfs_set_norm_projection": [vp, i32],
             "hfs_set_dft_engine": [vp, i32],
+            "hfs_set_schedule_reuse": [vp, i32],
             "hfs_set_graphs": [vp, i32],
             "hfs_set_time": [vp, dbl],
             "hfs_get_time": [vp, ctypes.POINTER(dbl)],
@@ -211,6 +213,15 @@ def hfs_set_norm_projection(h, enable: bool):
 
 def hfs_set_dft_engine(h, engine: int):
     _check(lib().hfs_set_dft_engine(h, int(engine)), "hfs_set_dft_engine")
+
+
+def hfs_set_schedule_reuse(h, enable: bool) -> int:
+    """Returns the status: HFS_OK, or HFS_ERR_WORKSPACE when the context was
+    left unbound for a larger workspace (other errors raise)."""
+    st = lib().hfs_set_schedule_reuse(h, 1 if enable else 0)
+    if st not in (0, HFS_ERR_WORKSPACE):
+        _check(st, "hfs_set_schedule_reuse")
+    return st
 
 
 def hfs_set_graphs(h, enable: bool):
@@ -358,6 +369,17 @@ class Solver:
 
     def set_dft_engine(self, engine: int):
         hfs_set_dft_engine(self.h, engine)
+
+    def set_schedule_reuse(self, enable: bool):
+        """Keep the phase records of the last calls and compute the next
+        call's in parallel with the step kernel (1D); re-binds with a larger
+        workspace when the current one has no room for the second buffer."""
+        torch = self._torch
+        with torch.cuda.device(self.device):
+            if hfs_set_schedule_reuse(self.h, enable) == HFS_ERR_WORKSPACE:
+                self.work_bytes = hfs_workspace_size(self.h, self.chunk_steps)
+                self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+                hfs_bind(self.h, self.psi.data_ptr(), self.work.data_ptr(), self.work_bytes, self.chunk_steps)
 
     def set_time(self, t: float):
         hfs_set_time(self.h, t)
