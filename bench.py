@@ -643,6 +643,9 @@ def run_case(args):
         X = S.features(bi, bp)
         Y = S.solve(bi, bp)
         m = Fno(FnoConfig(), max_batch=args.count, train=True, seed=7)
+        if args.tcgen05_gemm:
+            from paper_1007_3470_gb300.fno import HFS_FNO_GEMM_TCGEN05
+            m.set_gemm_engine(HFS_FNO_GEMM_TCGEN05)
         xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
         torch.cuda.synchronize()
         for _ in range(args.warmup):
@@ -655,7 +658,7 @@ def run_case(args):
         dt = (time.perf_counter() - t0) / args.steps
         rate = S.time_inference(m, X)
         m.close()
-        print(json.dumps({"case": "fno", "batch": args.count, "train_step_ms": dt * 1e3,
+        print(json.dumps({"case": "fno", "batch": args.count, "tcgen05_gemm": args.tcgen05_gemm, "train_step_ms": dt * 1e3,
                           "inference_samples_per_s": rate}))
     elif args.case == "hbm":
         print(json.dumps({"case": "hbm", **hbm_streaming_measurement(hfs, W, count=args.count,
@@ -717,6 +720,8 @@ def main():
                     help="skip the per-grid-size plan autotuner")
     ap.add_argument("--count", type=int, default=COUNT, help="instances per batch (profiling cases use fewer)")
     ap.add_argument("--time-steps", type=int, default=STEPS, help="time steps per solve")
+    ap.add_argument("--tcgen05-gemm", action="store_true",
+                    help="case fno: the row-streaming GEMMs on the tcgen05 engine")
     ap.add_argument("--tensor-dft", action="store_true",
                     help="--case 3d: the z-transforms' radix-16 stages on the tensor cores")
     ap.add_argument("--case", choices=["3d", "fno", "hbm"], default=None,

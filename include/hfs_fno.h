@@ -81,6 +81,26 @@ int hfs_fno_loss_grad(hfs_fno_t f, const float *x_dev, const float *y_dev, int32
 int hfs_fno_train_step(hfs_fno_t f, const float *x_dev, const float *y_dev, int32_t batch, float lr,
                        float *loss_host);
 
+/* GEMM engine of the row-streaming products (rows >= 8192, K and N of 64 or
+ * 128: the pointwise layers, the projection and their backward products).
+ * HFS_FNO_GEMM_MMA_SYNC (default): cp.async tile ring and mma.sync.m16n8k16.
+ * HFS_FNO_GEMM_TCGEN05: persistent CTAs keep op(B) in shared memory, stream
+ * 128-row tiles of A, and run the products on the tcgen05 tensor cores (BF16
+ * operands through shared-memory descriptors, FP32 accumulators in tensor
+ * memory, one tile's products issued while the previous tile's epilogue
+ * runs); at batch 512 it measures slower than the default (its per-tile
+ * phases are latency bound at three CTAs per SM).  Other shapes always use
+ * mma.sync.  Errors: HFS_ERR_INVALID_ARG. */
+#define HFS_FNO_GEMM_MMA_SYNC 0
+#define HFS_FNO_GEMM_TCGEN05 1
+int hfs_fno_set_gemm_engine(hfs_fno_t f, int engine);
+
+/* Wait for the context's stream and report device-side problems since the
+ * last call: HFS_ERR_DEVICE_TIMEOUT when a tensor-core GEMM's bounded wait
+ * for its matrix products ran out (that launch's results were not written);
+ * the word is cleared. */
+int hfs_fno_sync_status(hfs_fno_t f);
+
 #ifdef __cplusplus
 }
 #endif

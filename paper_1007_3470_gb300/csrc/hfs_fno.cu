@@ -12,6 +12,7 @@
 #include "hfs.h"
 #include "hfs_fno.h"
 #include "hfs_fno_kernels.cuh"
+#include "hfs_fno_tc.cuh"
 
 using namespace hfs::fno;
 
@@ -37,10 +38,11 @@ struct hfs_fno_s {
     unsigned char *work = nullptr;
     size_t work_bytes = 0;
     int64_t step = 0;
+    int gemm_engine = HFS_FNO_GEMM_MMA_SYNC;  // hfs_fno_set_gemm_engine
     // workspace sections (byte offsets)
     struct {
         size_t X8, Hf, Hb, pre, S, Yf, Yb, U, Qpre, Qb, O, dO, dOb, dQ, dQb, dH, dZ, dZb, dYb, dSb, dR1, dR2, grad, m,
-            v, sums, loss, Pinb, Wb, Rb1, Rb2, P1b, P2b, F2, Gre, Gim, total;
+            v, sums, loss, Pinb, Wb, Rb1, Rb2, P1b, P2b, F2, Gre, Gim, status, total;
     } off{};
 };
 
@@ -129,6 +131,7 @@ void layout(hfs_fno_s *f)
     w.F2 = take(2 * 2 * M * L);
     w.Gre = take(2 * L * M);
     w.Gim = take(2 * L * M);
+    w.status = take(4);
     w.total = o;
 }
 
@@ -156,8 +159,45 @@ GemmArgs gemm(int M, int N, int K, const bf16 *A, int64_t lda, const bf16 *B, in
     return g;
 }
 
-cudaError_t run(const GemmArgs &g, bool ta, bool tb, cudaStream_t st)
+// tensor-core form (hfs_fno_tc.cuh): persistent, as many CTAs per SM as the
+// shared and tensor memory hold
+template <bool TB, int NT, int KT> cudaError_t run_tc(const GemmArgs &g, cudaStream_t st)
 {
+    static int ctas = 0;  // CTAs of the grid per batch slice (SMs x resident CTAs), set once
+    auto k = gemm_bf16_tc_kernel<TB, NT, KT>;
+    constexpr int smem = tc_smem_bytes<NT, KT>();
+    if (ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int dev = 0, sms = 0, per = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 128, smem);
+        if (e != cudaSuccess) return e;
+        ctas = sms * std::max(1, std::min(per, 512 / (2 * NT)));  // tensor memory: two NT-column accumulators
+    }
+    const int tiles = (g.M + TC_M - 1) / TC_M;
+    k<<<dim3((unsigned)std::min(tiles, ctas), (unsigned)g.batch), 128, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+// status: the tensor-core form's status word; null selects the mma.sync forms
+cudaError_t run(const GemmArgs &g0, bool ta, bool tb, cudaStream_t st, unsigned *status = nullptr)
+{
+    GemmArgs g = g0;
+    g.status = status;
+    if (status && gemm_tc_ok(g, ta)) {
+        const int key = (tb ? 4 : 0) + (g.N == 128 ? 2 : 0) + (g.K == 128 ? 1 : 0);
+        switch (key) {
+        case 0: return run_tc<false, 64, 64>(g, st);
+        case 1: return run_tc<false, 64, 128>(g, st);
+        case 2: return run_tc<false, 128, 64>(g, st);
+        case 3: return run_tc<false, 128, 128>(g, st);
+        case 4: return run_tc<true, 64, 64>(g, st);
+        case 5: return run_tc<true, 64, 128>(g, st);
+        case 6: return run_tc<true, 128, 64>(g, st);
+        default: return run_tc<true, 128, 128>(g, st);
+        }
+    }
     const dim3 grid((g.N + GT_N - 1) / GT_N, (g.M + GT_M - 1) / GT_M, g.batch * g.splitk);
     if (gemm_pipe_ok(g, ta, tb)) {
         if (!ta && !tb) gemm_bf16_pipe_kernel<false, false><<<grid, 128, 0, st>>>(g);
@@ -217,6 +257,8 @@ int forward(hfs_fno_s *f, const float *x, int B)
     const int64_t L = c.grid, C = c.width, M = c.modes, P = c.proj, NL = c.layers;
     const int64_t rows = (int64_t)B * L, Bm = f->max_batch, rowsM = Bm * L;
     cudaStream_t st = f->stream;
+    // the tensor-core GEMMs' bounded-wait status word; null keeps every GEMM on mma.sync
+    unsigned *fst = f->gemm_engine == HFS_FNO_GEMM_TCGEN05 ? at<unsigned>(f, f->off.status) : nullptr;
     const auto &w = f->off;
     bf16 *X8 = at<bf16>(f, w.X8);
     to_bf16_pad_kernel<<<blocks(rows * kInPad), 256, 0, st>>>(x, rows, c.in_ch, X8, kInPad);
@@ -230,7 +272,7 @@ int forward(hfs_fno_s *f, const float *x, int B)
         g.ldc = C;
         g.Cb = Hb;
         g.ldcb = C;
-        FCK(run(g, false, false, st));
+        FCK(run(g, false, false, st, fst));
     }
     for (int l = 0; l < NL; ++l) {
         const bf16 *Hinb = Hb + l * rowsM * C;
@@ -244,7 +286,7 @@ int forward(hfs_fno_s *f, const float *x, int B)
             g.ldcb = C;
             g.sCb = 2 * M * C;
             g.batch = B;
-            FCK(run(g, false, false, st));
+            FCK(run(g, false, false, st, fst));
         }
         // Y_k = S_re,k R1_k + S_im,k R2_k   (B x 2C per mode)
         float *Yf = at<float>(f, w.Yf);
@@ -264,7 +306,7 @@ int forward(hfs_fno_s *f, const float *x, int B)
                 g.sCb = Bm * 2 * C;
             }
             g.batch = (int)M;
-            FCK(run(g, false, false, st));
+            FCK(run(g, false, false, st, fst));
         }
         // U_b = Gre Yre_b + Gim Yim_b   (L x C per sample)
         float *U = at<float>(f, w.U);
@@ -278,7 +320,7 @@ int forward(hfs_fno_s *f, const float *x, int B)
             g.sC = L * C;
             g.beta = part;
             g.batch = B;
-            FCK(run(g, false, false, st));
+            FCK(run(g, false, false, st, fst));
         }
         // Z = H W + b + U; H_next = GELU(Z) (identity on the last layer)
         {
@@ -293,7 +335,7 @@ int forward(hfs_fno_s *f, const float *x, int B)
             g.ldc = C;
             g.Cb = Hb + (l + 1) * rowsM * C;
             g.ldcb = C;
-            FCK(run(g, false, false, st));
+            FCK(run(g, false, false, st, fst));
         }
     }
     // projection: Q = GELU(H P1 + c1); O = Q P2 + c2
@@ -305,14 +347,14 @@ int forward(hfs_fno_s *f, const float *x, int B)
         g.gelu = 1;
         g.Cb = at<bf16>(f, w.Qb);
         g.ldcb = P;
-        FCK(run(g, false, false, st));
+        FCK(run(g, false, false, st, fst));
     }
     {
         GemmArgs g = gemm((int)rows, c.out_ch, (int)P, at<bf16>(f, w.Qb), P, at<bf16>(f, w.P2b), c.out_ch);
         g.bias = f->params + f->po.c2;
         g.C = at<float>(f, w.O);
         g.ldc = c.out_ch;
-        FCK(run(g, false, false, st));
+        FCK(run(g, false, false, st, fst));
     }
     return HFS_OK;
 }
@@ -323,6 +365,8 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
     const int64_t L = c.grid, C = c.width, M = c.modes, P = c.proj, NL = c.layers, OC = c.out_ch;
     const int64_t rows = (int64_t)B * L, Bm = f->max_batch, rowsM = Bm * L;
     cudaStream_t st = f->stream;
+    // the tensor-core GEMMs' bounded-wait status word; null keeps every GEMM on mma.sync
+    unsigned *fst = f->gemm_engine == HFS_FNO_GEMM_TCGEN05 ? at<unsigned>(f, f->off.status) : nullptr;
     const auto &w = f->off;
     FCK(cudaMemsetAsync(grad, 0, 4 * f->nparams, st));
     // loss and dO
@@ -341,7 +385,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
         GemmArgs g = gemm((int)rows, (int)P, (int)OC, dOb, OC, at<bf16>(f, w.P2b), OC);  // dQ = dO P2^T
         g.C = dQ;
         g.ldc = P;
-        FCK(run(g, false, true, st));
+        FCK(run(g, false, true, st, fst));
     }
     gelu_bwd_kernel<<<blocks(rows * P), 256, 0, st>>>(dQ, at<float>(f, w.Qpre), 1, dQ, dQb, rows * P);
     bf16 *Hb = at<bf16>(f, w.Hb);
@@ -353,7 +397,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
         GemmArgs g = gemm((int)rows, (int)C, (int)P, dQb, P, at<bf16>(f, w.P1b), P);  // dH = dQpre P1^T
         g.C = dH;
         g.ldc = C;
-        FCK(run(g, false, true, st));
+        FCK(run(g, false, true, st, fst));
     }
     bf16 *dYb = at<bf16>(f, w.dYb), *dSb = at<bf16>(f, w.dSb);
     float *dR1 = at<float>(f, w.dR1), *dR2 = at<float>(f, w.dR2);
@@ -367,7 +411,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
             GemmArgs g = gemm((int)rows, (int)C, (int)C, dZb, C, at<bf16>(f, w.Wb) + l * C * C, C);  // dZ W^T
             g.C = dH;
             g.ldc = C;
-            FCK(run(g, false, true, st));
+            FCK(run(g, false, true, st, fst));
         }
         // dYre_b = Gre^T dU_b, dYim_b = Gim^T dU_b  -> dY[k][b][part C + o]
         for (int part = 0; part < 2; ++part) {
@@ -378,7 +422,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
             g.ldcb = Bm * 2 * C;
             g.sCb = 2 * C;
             g.batch = B;
-            FCK(run(g, true, false, st));
+            FCK(run(g, true, false, st, fst));
         }
         const bf16 *S = at<bf16>(f, w.S) + l * Bm * 2 * M * C;
         for (int part = 0; part < 2; ++part) {
@@ -390,7 +434,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
             g.ldc = 2 * C;
             g.sC = C * 2 * C;
             g.batch = (int)M;
-            FCK(run(g, true, false, st));
+            FCK(run(g, true, false, st, fst));
             // dS_{re,im},k = dY_k R{1,2}_k^T   -> dS[b][part M + k][c]
             GemmArgs h = gemm(B, (int)C, (int)(2 * C), dYb, 2 * C,
                               at<bf16>(f, part == 0 ? w.Rb1 : w.Rb2) + l * M * C * 2 * C, 2 * C);
@@ -400,7 +444,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
             h.ldcb = 2 * M * C;
             h.sCb = C;
             h.batch = (int)M;
-            FCK(run(h, false, true, st));
+            FCK(run(h, false, true, st, fst));
         }
         mixing_grad_kernel<<<blocks(M * C * C), 256, 0, st>>>(dR1, dR2, (int)M, (int)C, grad + f->po.Rre[l],
                                                                 grad + f->po.Rim[l]);
@@ -414,7 +458,7 @@ int backward(hfs_fno_s *f, const float *y, int B, float *grad)
             g.sC = L * C;
             g.beta = 1;
             g.batch = B;
-            FCK(run(g, true, false, st));
+            FCK(run(g, true, false, st, fst));
         }
     }
     // lift
@@ -493,7 +537,26 @@ int hfs_fno_bind(hfs_fno_t f, float *params, void *work, size_t work_bytes)
         FCK(cudaMemsetAsync(at<float>(f, f->off.v), 0, 4 * f->nparams, f->stream));
     }
     f->step = 0;
+    FCK(cudaMemsetAsync(at<unsigned>(f, f->off.status), 0, sizeof(unsigned), f->stream));
     return refresh_weights(f);
+}
+
+int hfs_fno_set_gemm_engine(hfs_fno_t f, int engine)
+{
+    if (!f || (engine != HFS_FNO_GEMM_MMA_SYNC && engine != HFS_FNO_GEMM_TCGEN05)) return HFS_ERR_INVALID_ARG;
+    f->gemm_engine = engine;
+    return HFS_OK;
+}
+
+int hfs_fno_sync_status(hfs_fno_t f)
+{
+    if (!f || !f->work) return HFS_ERR_NOT_READY;
+    unsigned word = 0;
+    unsigned *dev = at<unsigned>(f, f->off.status);
+    FCK(cudaMemcpyAsync(&word, dev, sizeof(unsigned), cudaMemcpyDeviceToHost, f->stream));
+    FCK(cudaStreamSynchronize(f->stream));
+    if (word) FCK(cudaMemsetAsync(dev, 0, sizeof(unsigned), f->stream));
+    return word ? HFS_ERR_DEVICE_TIMEOUT : HFS_OK;
 }
 
 int hfs_fno_init_params(hfs_fno_t f, uint64_t seed)

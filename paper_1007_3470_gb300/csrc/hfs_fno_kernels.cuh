@@ -33,6 +33,7 @@ struct GemmArgs {
     int64_t ldadd, sAdd;
     float alpha;
     int beta, gelu, splitk, batch;
+    unsigned *status;  // bit 0 set when a bounded device wait ran out (tensor-core form)
 };
 
 constexpr int GT_M = 64, GT_N = 64, GT_K = 32, GT_LD = 40;  // smem rows padded to 40 bf16 (80 B)

@@ -10,7 +10,9 @@ from . import hfs
 
 EXPORTS = ("hfs_fno_create", "hfs_fno_destroy", "hfs_fno_set_stream", "hfs_fno_param_count",
            "hfs_fno_workspace_size", "hfs_fno_bind", "hfs_fno_init_params", "hfs_fno_forward",
-           "hfs_fno_loss_grad", "hfs_fno_train_step")
+           "hfs_fno_loss_grad", "hfs_fno_train_step", "hfs_fno_set_gemm_engine",
+           "hfs_fno_sync_status")
+HFS_FNO_GEMM_MMA_SYNC, HFS_FNO_GEMM_TCGEN05 = 0, 1
 
 
 class hfs_fno_config(ctypes.Structure):
@@ -52,6 +54,8 @@ def _lib():
             "hfs_fno_forward": [vp, vp, vp, i32],
             "hfs_fno_loss_grad": [vp, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_float)],
             "hfs_fno_train_step": [vp, vp, vp, i32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)],
+            "hfs_fno_set_gemm_engine": [vp, i32],
+            "hfs_fno_sync_status": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -135,6 +139,13 @@ class Fno:
                                          x.shape[0], lr, ctypes.byref(loss) if want_loss else None),
                "hfs_fno_train_step")
         return loss.value if want_loss else None
+
+    def set_gemm_engine(self, engine: int):
+        _check(_lib().hfs_fno_set_gemm_engine(self.h, int(engine)), "hfs_fno_set_gemm_engine")
+
+    def status(self) -> int:
+        """Device-side status since the last call (0, or HFS_ERR_DEVICE_TIMEOUT = 9)."""
+        return _lib().hfs_fno_sync_status(self.h)
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -78,3 +78,31 @@ def test_adam_training_reduces_loss():
         last = m.train_step(xd, yd, 3e-3)
     assert last < 0.5 * first, (first, last)
     m.close()
+
+
+def test_tensor_core_gemms_forward_and_gradients():
+    """With the tcgen05 engine, rows >= 8192 with widths of 64 and 128 take
+    the tensor-core GEMMs (operands in shared memory, accumulators in tensor
+    memory): the pointwise layers (K = N = 64, B plain and transposed in the
+    backward pass), the projection (N = 128) and its backward product
+    (K = 128).  64 x 129 rows leave the last 128-row tile ragged.  Same bounds
+    as the mma.sync path above, and no bounded wait runs out."""
+    torch = need_gpu()
+    cfgref = F.Config(L=64, C=64, M=8, layers=2, in_ch=7, P=128, out=2)
+    B = 129
+    from paper_1007_3470_gb300.fno import HFS_FNO_GEMM_TCGEN05
+    m, p = _model(cfgref, B)
+    m.set_gemm_engine(HFS_FNO_GEMM_TCGEN05)
+    X, Y = _data(cfgref, B)
+    out = m.forward(torch.from_numpy(X.astype(np.float32))).cpu().numpy()
+    assert _rel(out, F.forward(cfgref, p, X)) < 3e-2
+    loss, g = m.loss_grad(torch.from_numpy(X.astype(np.float32)), torch.from_numpy(Y.astype(np.float32)))
+    lref, gref = F.loss_and_grad(cfgref, p, X, Y)
+    assert abs(loss - lref) < 2e-2 * lref
+    gg = F.unpack(cfgref, g.cpu().numpy().astype(np.float64))
+    for name, _ in cfgref.shapes():
+        assert _rel(gg[name], gref[name]) < 0.1, name
+    a, b = g.cpu().numpy().astype(np.float64), F.pack(cfgref, gref)
+    assert float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b))) > 0.995
+    assert m.status() == 0
+    m.close()
