@@ -239,6 +239,14 @@ def extra_measurements(hfs, W, torch):
         "kernel_ms": ms_tc, "grid_point_steps_per_s": gps / (ms_tc * 1e-3),
         "dft_stages": "radix-16 z-pass stages as 3xTF32 tcgen05 matrix products",
         "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
+    # tensor-core stages with the norm projection (which removes their norm bias)
+    s3.set_norm_projection(True)
+    s3.set_time(0.0)
+    s3.set_psi(psi0.ravel())
+    ms_tcp = kernel_ms(s3, steps)
+    out["gpe3d_128cube_200steps_c64_tensor_dft_projected"] = {
+        "kernel_ms": ms_tcp, "grid_point_steps_per_s": gps / (ms_tcp * 1e-3),
+        "error": gpe3d_error(hfs, s3, inst, psi0, steps)}
     s3.close()
     # streaming mode of the batched workload (one launch per time step)
     insts, psis, _ = W.batch_1d(count=COUNT, h=DT, steps=STEPS)

@@ -314,7 +314,7 @@ int hfs_last_step_kernel_ms(hfs_ctx_t ctx, float *ms);
  * file-scope __device__ array of HFS_NOALLOC_SCRATCH_BYTES that every GPU
  * loading the library keeps until process exit.  The first call on a device
  * resolves the array's address and fills its twiddle tables, synchronising
- * the stream; make that first call before any stream capture.  Every call
+ * the stream.  Every call
  * reuses the same array, which keeps the previous call's contents (the call
  * clears what must start at zero): calls whose GPU work overlaps -- on
  * different streams, or from different host threads -- race on it and must

@@ -89,7 +89,7 @@ int hfs_fno_train_step(hfs_fno_t f, const float *x_dev, const float *y_dev, int3
  * operands through shared-memory descriptors, FP32 accumulators in tensor
  * memory, one tile's products issued while the previous tile's epilogue
  * runs); at batch 512 it measures slower than the default (its per-tile
- * phases are latency bound at three CTAs per SM).  Other shapes always use
+ * phases are latency bound with few warps per SM).  Other shapes always use
  * mma.sync.  Errors: HFS_ERR_INVALID_ARG. */
 #define HFS_FNO_GEMM_MMA_SYNC 0
 #define HFS_FNO_GEMM_TCGEN05 1
