@@ -8,9 +8,10 @@
 // memory for the whole launch and streams 128-row tiles of A through a
 // two-stage ring of 16-byte asynchronous copies; one thread issues the K / 16
 // MMAs of a tile (M = 128, N, K = 16, BF16 operands from shared memory, FP32
-// accumulator in tensor memory) and commits them to an mbarrier, and each
-// thread then reads its row of the accumulator (tcgen05.ld) and applies the
-// epilogue while the next tile's copies are in flight.  Both operands are
+// accumulator in one of two tensor-memory buffers) and commits them to that
+// buffer's mbarrier, so that tile j + 1's products and tile j + 2's copies
+// are in flight while the warps read tile j's accumulator back (tcgen05.ld)
+// and apply the epilogue.  Both operands are
 // stored K-major without swizzle: core matrices of 8 rows x 16 bytes, the
 // core matrices adjacent in K 128 bytes apart (leading byte offset) and the
 // 8-row groups K x 16 bytes apart (stride byte offset).  The one wait, for

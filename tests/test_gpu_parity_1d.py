@@ -191,6 +191,27 @@ def test_mixed_perturbations_and_boxes_in_one_batch(precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
+def test_cos_perturbation_far_from_the_centre(precision, tol):
+    """eps cos(k x) where |k x| reaches a few hundred radians under the state:
+    a packet at x0 = 55 in a weak trap, k = 4, on a symmetric box (the
+    kernel specialised for cos) and on a box centred at 40 (the generic
+    kernel, whose table adds k x_c / 2 pi mod 1).  A large eps makes the
+    perturbation's phase dominate the error budget."""
+    need_gpu()
+    insts, psis = [], []
+    for lo, hi in ((-72.0, 72.0), (-32.0, 112.0)):
+        inst = W.Instance(n=[4096], a=[lo], b=[hi], omega_law=W.OMEGA_SIN, w0=0.05, law=[0.3, 1.0, 0.0],
+                          eps=0.8, vi_kind=W.VI_COS, vi_k=4.0, sigma=2.0, ho_flow=W.FLOW_CF4, h=0.005)
+        insts.append(inst)
+        psis.append(W.gaussian_1d(inst, x0=55.0, width2=4.0, p0=0.3))
+    steps = 300
+    outs = _run_gpu(insts, psis, steps, precision, insts[0].h)
+    for inst, p0, out in zip(insts, psis, outs):
+        ref = O.run(O.Problem(**inst.as_dict()), p0, steps)
+        assert O.rel_l2(out, ref) <= budget(tol, steps * inst.h)
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", TOL_C128), ("c64", TOL_C64)])
 def test_asymmetric_box_and_mass(precision, tol):
     """A box not centred at 0 (K1, K0 terms of the chirp) and mu != 1."""
     need_gpu()
