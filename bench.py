@@ -537,7 +537,7 @@ def run_native(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / alu_peak, "traffic": step1d_traffic(workload),
                      "traffic_note": "DRAM bytes per launch (ncu); the state stays on chip for all time "
-                                     "steps, the rest is schedule records and spill write-back",
+                                     "steps, the rest is the FP32 phase records (no register spills)",
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz {src})",
                      "hbm_equivalent_GBps": hbm_equiv, "hbm_equivalent_frac_of_measured": hbm_equiv / hbm},
         "e2e": {"value": gps_all / (e2e_step_ms * 1e-3), "unit": "grid-point-steps/s",
