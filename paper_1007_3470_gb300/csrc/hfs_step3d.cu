@@ -112,6 +112,16 @@ __global__ void __launch_bounds__(kCtaThreads) ypass3d(const Step3DArgs a)
     for (int e = 0; e < E; ++e) psi[(int64_t)(t + T * e) * N] = v[e];
 }
 
+// Programmatic dependent launch of the 128^3 chain (z-pass, plane pass, ...):
+// a kernel launched with programmatic stream serialisation may start while
+// its predecessor finishes; pdl_wait() returns once the predecessor has
+// completed and its memory is visible (at once for a kernel launched
+// normally), and pdl_trigger() lets the successor be scheduled as soon as
+// every CTA of this grid has started.  Nothing before pdl_wait() reads or
+// writes the state or the projection sums.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // z-pass: one CTA = fixed y, TX adjacent x columns; forward FFT_z, k-phase,
 // inverse FFT_z
@@ -166,6 +176,8 @@ __global__ void __launch_bounds__(kCtaThreads, ZpassMinCtas<R>::value) zpass3d(c
     const int y = blockIdx.y, x = blockIdx.x * TX + l;
     cpx<R> *sm = reinterpret_cast<cpx<R> *>(smem_raw) + l;
     cpx<R> *psi = reinterpret_cast<cpx<R> *>(a.psi) + (int64_t)y * N + x;
+    pdl_wait();
+    pdl_trigger();
     cpx<R> v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = psi[(int64_t)(t + T * e) * N * N];
@@ -245,6 +257,8 @@ __global__ void __launch_bounds__(kCtaThreads, 2) zpass3d_tc(const Step3DArgs a,
     __syncthreads();
     tc::fence_after_sync();
     tc::Dft16 st{*slot, tc::smem_addr(wbuf), tc::smem_addr(wbuf + tc::kWBytes), tc::smem_addr(mbar), 0u};
+    pdl_wait();
+    pdl_trigger();
 
     const int l = threadIdx.x % TX, t = threadIdx.x / TX;
     const int y = blockIdx.y, x = blockIdx.x * TX + l;
@@ -314,6 +328,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
         for (int i = threadIdx.x; i < N; i += kPlaneThreads)
             s_vx[i] = (float)ip.eps * vi_eval(VI, (float)(i - N / 2) * (float)ip.dx[0], (float)ip.vi_k);
     }
+    pdl_wait();
+    pdl_trigger();
     const int z = blockIdx.x;
     cpx<float> *psi = reinterpret_cast<cpx<float> *>(a.psi) + (int64_t)z * N * N;
     // With the inverse y-transform the columns come straight from global
@@ -351,7 +367,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) plane3d(const Step3DArgs a, 
         const Rec3F rc = reinterpret_cast<const Rec3F *>(a.rec)[j];
         const int mz = z - N / 2;
         constexpr int vkind = VI;
-        const float dx = (float)ip.dx[0], vk = (float)ip.vi_k, eps = (float)ip.eps, sig = (float)ip.sigma;
+        const float vk = (float)ip.vi_k, eps = (float)ip.eps, sig = (float)ip.sigma;
         const float tz = turns_q(mz, rc.k2[2], rc.k2lo[2]);
         const float vz = vi_eval(vkind, (float)mz * (float)ip.dx[2], vk);
         for (int r = 0; r < N / LINES; ++r) {
@@ -544,6 +560,24 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// launch with programmatic stream serialisation (see pdl_wait)
+template <typename... P>
+static cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              const Step3DArgs &a, int64_t j)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a, j);
+}
+
 template <typename R, int N> static cudaError_t run3d(const Step3DArgs &a, cudaStream_t st)
 {
     using GEO = Geo3<N>;
@@ -621,14 +655,18 @@ template <int VI, bool PROJ> static cudaError_t run3d_plane_vi(const Step3DArgs 
         prepared = true;
     }
     const dim3 tg(N / GEO::TX, N);
+    // the first plane pass follows the schedule kernels and the sums' reset
+    // in plain stream order; every later launch overlaps its predecessor's end
     plane3d<FIRST, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, 0);
-    for (int64_t j = 0; j < a.nstage; ++j) {
-        if (a.dft_tc) zpass3d_tc<N, PROJ><<<tg, GEO::TT, zpass_tc_smem<N>(), st>>>(a, j);
-        else zpass3d<float, N, PROJ><<<tg, GEO::TT, ts, st>>>(a, j);
-        if (j + 1 < a.nstage) plane3d<MID, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
-        else plane3d<LAST, VI, PROJ><<<N, kPlaneThreads, ps, st>>>(a, j + 1);
+    cudaError_t e = cudaGetLastError();
+    for (int64_t j = 0; j < a.nstage && e == cudaSuccess; ++j) {
+        if (a.dft_tc) e = launch_pdl(zpass3d_tc<N, PROJ>, tg, dim3(GEO::TT), zpass_tc_smem<N>(), st, a, j);
+        else e = launch_pdl(zpass3d<float, N, PROJ>, tg, dim3(GEO::TT), ts, st, a, j);
+        if (e != cudaSuccess) break;
+        if (j + 1 < a.nstage) e = launch_pdl(plane3d<MID, VI, PROJ>, dim3(N), dim3(kPlaneThreads), ps, st, a, j + 1);
+        else e = launch_pdl(plane3d<LAST, VI, PROJ>, dim3(N), dim3(kPlaneThreads), ps, st, a, j + 1);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 static cudaError_t run3d_plane(const Step3DArgs &a, cudaStream_t st)
