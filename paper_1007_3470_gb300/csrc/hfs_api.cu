@@ -551,7 +551,7 @@ int hfs_create(hfs_ctx_t *out, int dim, int precision, const hfs_instance *inst,
         d.vi_k = p.vi_k;
         d.sigma = p.sigma;
         d.plan = (dim == 1) ? size_class(p.n[0]) : 0;
-        if (dim == 1) set_vi_turns(d);
+        if (dim == 1) set_1d_fp32_params(d);
     }
     c->elems = off;
     if (dim == 1) build_worklist(c);

@@ -79,11 +79,23 @@ struct DevInst {
     // 1D, V_I = cos(k x): k x / (2 pi) in turns as (a_hi + a_lo) + (b_hi + b_lo) m
     // for x = xc + m dx (a = k xc / (2 pi) mod 1, b = k dx / (2 pi)), FP32 pairs
     float vi_turns[4];
+    // 1D FP32 kernels: xc, dx, eps, vi_k, sigma rounded to FP32, the
+    // perturbation kind in effect (none where eps = 0) and whether xc != 0
+    float f32[5];
+    int32_t vi_kind_eff, asym;
 };
 
-// vi_turns of a 1D instance from its FP64 parameters (host)
-inline void set_vi_turns(DevInst &d)
+// vi_turns and the FP32 copies of a 1D instance from its FP64 parameters
+// (host; the same roundings as converting on the device)
+inline void set_1d_fp32_params(DevInst &d)
 {
+    d.f32[0] = (float)d.xc[0];
+    d.f32[1] = (float)d.dx[0];
+    d.f32[2] = (float)d.eps;
+    d.f32[3] = (float)d.vi_k;
+    d.f32[4] = (float)d.sigma;
+    d.vi_kind_eff = d.eps != 0.0 ? d.vi_kind : HFS_VI_NONE;
+    d.asym = d.xc[0] != 0.0 ? 1 : 0;
     const double inv_2pi = 0.159154943091895335768883763372514362;
     const double b = d.vi_k * d.dx[0] * inv_2pi;
     double a = d.vi_k * d.xc[0] * inv_2pi;

@@ -137,7 +137,7 @@ extern "C" int hfs_step1d_noalloc(void *psi, int precision, const hfs_instance *
         d.eps = p.eps;
         d.vi_k = p.vi_k;
         d.sigma = p.sigma;
-        set_vi_turns(d);
+        set_1d_fp32_params(d);
         off += n;
     }
     if (nsteps == 0) return HFS_OK;

@@ -39,13 +39,24 @@ template <typename R> struct TeamParams {
 template <typename R> __device__ __forceinline__ TeamParams<R> team_params(const DevInst &p)
 {
     TeamParams<R> tp;
-    tp.xc = (R)p.xc[0];
-    tp.dx = (R)p.dx[0];
-    tp.eps = (R)p.eps;
-    tp.vik = (R)p.vi_k;
-    tp.sigma = (R)p.sigma;
-    tp.vikind = (p.eps != 0.0) ? p.vi_kind : HFS_VI_NONE;
-    tp.asym = (p.xc[0] != 0.0);
+    if constexpr (sizeof(R) == 4) {
+        // rounded on the host: no FP64 conversions per work item
+        tp.xc = p.f32[0];
+        tp.dx = p.f32[1];
+        tp.eps = p.f32[2];
+        tp.vik = p.f32[3];
+        tp.sigma = p.f32[4];
+        tp.vikind = p.vi_kind_eff;
+        tp.asym = p.asym != 0;
+    } else {
+        tp.xc = (R)p.xc[0];
+        tp.dx = (R)p.dx[0];
+        tp.eps = (R)p.eps;
+        tp.vik = (R)p.vi_k;
+        tp.sigma = (R)p.sigma;
+        tp.vikind = (p.eps != 0.0) ? p.vi_kind : HFS_VI_NONE;
+        tp.asym = (p.xc[0] != 0.0);
+    }
     tp.vt_b[0] = p.vi_turns[0];
     tp.vt_b[1] = p.vi_turns[1];
     tp.vt_a[0] = p.vi_turns[2];
