@@ -56,9 +56,9 @@ def tune(solver, trial_steps):
 # DRAM bytes per launch of the fused step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same command, summarised in
 # profiles/), valid only while the kernel's sources hash to "src".
-STEP1D_TRAFFIC = {"src": "062612c76e6dd54d",
-                  "batch_1d_4096x500_c64": 109656576 + 16323072,
-                  "batch_1d_65536x1_streaming": (727465728 + 648221952 + 727444736 + 645138688) // 2}
+STEP1D_TRAFFIC = {"src": "88d5e6598e9904c5",
+                  "batch_1d_4096x500_c64": 109323520 + 16402432,
+                  "batch_1d_65536x1_streaming": (727424512 + 646248960 + 727406080 + 643721728) // 2}
 STEP1D_SOURCES = ("hfs_step1d.cuh", "hfs_step1d.cu", "hfs_step1d_vicos.cu", "hfs_step1d_vix4.cu", "hfs_step1d_vinone.cu",
                   "hfs_step1d_wide.cu", "hfs_step1d_wide_vicos.cu", "hfs_step1d_wide_vix4.cu",
                   "hfs_step1d_wide_vinone.cu", "hfs_fft.cuh", "hfs_phase.cuh", "hfs_internal.cuh", "hfs_sched.h")
